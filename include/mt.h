@@ -1,0 +1,201 @@
+/*
+ * mt.h -- C ABI of the GB300 MetaTrinity hot path (seed -> count -> locate -> SneakySnake ->
+ * abundance), after Gollwitzer et al., "MetaTrinity: Enabling Fast Metagenomic
+ * Classification via Seed Counting and Edit Distance Approximation", arXiv 2311.02029.
+ *
+ * Conventions shared by every call:
+ *  - Bases are upper-case ASCII A, C, G, T (Methods: the DNA alphabet). Any other byte,
+ *    including N, makes a call fail with MT_EINVAL.
+ *  - Sequence sets are one concatenated byte buffer plus uint64 offsets of length count+1
+ *    (offsets[0] may be non-zero; sequence i is bytes [offsets[i], offsets[i+1])).
+ *  - 2-bit packed sequences: base j of a sequence sits at bits 2*(j%32) .. 2*(j%32)+1 of
+ *    word j/32 (codes A=0, C=1, G=2, T=3; unused high bits are zero). Sequence i of a set
+ *    whose base offsets are off[] starts at word (off[i] >> 5) + i, so packed sets need
+ *    (off[n] >> 5) + n + 1 words and no separate word-offset table.
+ *  - Ownership: inputs are borrowed for the duration of the call; output buffers are owned
+ *    by the caller; mt_index and mt_server objects are owned by the library until freed.
+ *  - Errors: every call returns MT_OK (0) or a negative status (below). No call aborts the
+ *    process; after an error the contents of output buffers are unspecified.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls that return results to the host synchronise that stream before returning.
+ */
+#ifndef MT_H_
+#define MT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define MT_OK 0
+#define MT_EINVAL (-1)      /* bad base, bad offsets, parameter out of range */
+#define MT_ENOMEM (-2)      /* device or host allocation failed / over budget */
+#define MT_ETIMEDOUT (-3)   /* a bounded wait ran out */
+#define MT_ECUDA (-4)       /* a CUDA runtime error (see mt_last_cuda_error) */
+#define MT_ECANCELED (-5)   /* a serving request was cancelled */
+#define MT_EBUSY (-6)       /* a serving request is still in flight */
+
+/* ---- limits ---------------------------------------------------------------------------- */
+#define MT_MAX_READ_LEN 1024u   /* bases per read (the paper targets short reads) */
+#define MT_MAX_K 31u            /* k-mer length; codes use 2k <= 62 bits */
+#define MT_MAX_W 64u            /* k-mers per minimizer window */
+#define MT_MAX_E 127u           /* edit threshold; 2E+1 <= 255 diagonals */
+#define MT_MAX_TOPN 8u          /* mapping locations kept per read */
+#define MT_MAX_OCC_LIMIT 2048u  /* largest accepted max_occ */
+#define MT_MAX_GENOMES (1u << 30)
+
+typedef struct mt_index mt_index;     /* opaque device-resident reference index */
+typedef struct mt_server mt_server;   /* opaque continuous-batching request loop */
+
+/* Index parameters (Results, "Evaluation Methodology": minimap2 short-read seeds; the
+ * paper's containment index uses k = 28, w = 18; the workloads here use k15/w10, k21/w11). */
+typedef struct {
+    uint32_t k;          /* k-mer length, 1..MT_MAX_K */
+    uint32_t w;          /* consecutive k-mers per window, 1..MT_MAX_W */
+    uint32_t canonical;  /* 1: a k-mer and its reverse complement share one code */
+    uint32_t reserved;   /* must be 0 */
+} mt_index_params;
+
+/* Per-call classification parameters. Paper defaults in brackets. */
+typedef struct {
+    uint32_t e_abs;        /* edit threshold E in bases, used when e_permille == 0 */
+    uint32_t e_permille;   /* E(n) = floor(n * e_permille / 1000)  [10% of the read length] */
+    uint32_t min_seeds;    /* minimum seed hits per mapping location  [3] */
+    uint32_t top_n;        /* locations per read kept for the approximation  [3] */
+    uint32_t max_occ;      /* seeds with more occurrences are skipped  [1024] */
+    uint32_t cont_num;     /* containment cutoff num/den on hits/max_hits  [1/10000] */
+    uint32_t cont_den;
+    uint32_t eda_mode;     /* MT_EDA_BATCHED or MT_EDA_PLAIN (identical results) */
+    double abund_cutoff;   /* relative abundances below this are dropped  [1e-4] */
+} mt_classify_params;
+
+#define MT_EDA_BATCHED 0u  /* persistent work-stealing kernel, autotuned group shape */
+#define MT_EDA_PLAIN 1u    /* one warp per pair, one launch per length bucket */
+
+/* One mapping location of a read (24 bytes). */
+typedef struct {
+    int64_t wstart;   /* reference window start, forward strand: first diagonal - E */
+    int32_t genome;   /* genome index, -1 for an unused slot */
+    uint32_t seeds;   /* seed hits of the location */
+    uint8_t strand;   /* 1: the read matches the genome's reverse strand */
+    uint8_t dist;     /* SneakySnake distance, capped at E + 1 (E + 1 = rejected) */
+    uint8_t pad[6];
+} mt_loc;
+
+/* Optional per-call counters. */
+typedef struct {
+    uint64_t n_reads;
+    uint64_t n_minimizers;   /* read minimizers looked up */
+    uint64_t n_hits;         /* seed matches (all genomes) */
+    uint64_t n_candidates;   /* locations sent to the approximation */
+    uint64_t n_accepted;     /* reads with a location at distance <= E */
+    uint64_t n_multi;        /* accepted reads whose best distance is shared by >1 genome */
+    uint64_t n_fallback;     /* reads re-mapped by the exact slow path (hit overflow) */
+    uint64_t workspace_bytes;
+} mt_stats;
+
+typedef struct {
+    uint32_t n_genomes, k, w, canonical;
+    uint64_t total_bases;
+    uint64_t n_occ;          /* genome minimizers stored */
+    uint64_t n_keys;         /* distinct minimizer codes */
+    uint64_t table_slots;    /* open-addressing slots (power of two) */
+    uint64_t device_bytes;   /* HBM held by the index */
+} mt_index_info;
+
+/* ---- general ---------------------------------------------------------------------------- */
+const char *mt_strerror(int status);
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char *mt_last_cuda_error(void);
+int mt_version(void);
+
+/* ---- index (Methods, "Reference Database Organisation and Index Construction &
+ * Querying"): every genome's (w,k)-minimizers, key = SplitMix64 finaliser of the k-mer
+ * code, held in HBM as an open-addressing table of 32-byte slots (one DRAM sector per
+ * probe; up to three occurrences inline) plus an occurrence array sorted by
+ * (code, genome, position). The 2-bit packed genomes stay resident for the
+ * reference windows of the edit-distance approximation.
+ *
+ * genomes/offsets: HOST buffers, n_genomes sequences, each shorter than 2^32 bases.
+ * stream: used for the build; the call returns after the build completes.
+ * Errors: MT_EINVAL (bad base, k/w out of range, empty set), MT_ENOMEM, MT_ECUDA. */
+int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
+                   const mt_index_params *params, void *stream, mt_index **out);
+void mt_free_index(mt_index *ix);
+int mt_index_get_info(const mt_index *ix, mt_index_info *info);
+
+/* ---- classification of one read batch (Fig. 1 stages 1-3; "The MetaTrinity Pipeline"):
+ *  1. containment: minimizers of every read are looked up; hits are counted per genome
+ *     over the whole batch; genome g is kept iff hits[g]/max(hits) > cont_num/cont_den;
+ *  2. read mapping: per read, seed matches in kept genomes grouped into locations (one per
+ *     genome, strand and diagonal band of width E); locations with < min_seeds seeds
+ *     dropped, the top_n by seed count compared with SneakySnake against the reference
+ *     window [first diagonal - E, first diagonal + n + E); locations at distance <= E are
+ *     accepted;
+ *  3. profiling: a read whose best accepted distance belongs to one genome is unique; one
+ *     shared by several genomes is split in proportion to their unique counts (equally if
+ *     they have none); relative abundances below abund_cutoff are dropped and the rest
+ *     renormalised.
+ * reads: a buffer of n_bases bytes; offsets: n_reads + 1 non-decreasing entries with
+ *   offsets[n_reads] <= n_bases (read i is bytes [offsets[i], offsets[i+1]) of `reads`).
+ * device_ptrs: 1 = reads, offsets and every output pointer are device pointers (the call
+ *   still synchronises `stream` before returning, to report input errors); 0 = all are
+ *   host pointers (copies are made on `stream`).
+ * Outputs (any may be NULL except taxon): taxon[n_reads] (genome or -1);
+ *   nloc[n_reads]; locs[n_reads * top_n] (unused slots have genome -1);
+ *   genome_hits[n_genomes] (stage-1 counts); abundance[n_genomes]; stats.
+ * Errors: MT_EINVAL (bad base, read longer than MT_MAX_READ_LEN, bad offsets, parameter
+ *   out of range), MT_ENOMEM, MT_ECUDA. */
+int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
+                const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
+                int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                uint64_t *genome_hits, double *abundance, mt_stats *stats);
+
+/* Device bytes of scratch that one mt_classify call needs for this batch shape
+ * (inputs and outputs not included). Used for admission control. */
+uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
+                                     const mt_classify_params *params);
+
+/* ---- 2-bit packing (used by the seeding kernels; exposed for the EDA batch call) ---------
+ * seq/offsets/words: DEVICE pointers. Writes sequence i at word (offsets[i] >> 5) + i;
+ * words must hold (offsets[n_seqs] >> 5) + n_seqs + 1 entries. Errors: MT_EINVAL (non-ACGT
+ * byte; checked after a stream synchronisation), MT_ECUDA. */
+int mt_pack_seqs(const uint8_t *seq, const uint64_t *offsets, uint64_t n_seqs, uint64_t *words,
+                 void *stream);
+
+/* ---- edit-distance approximation stage alone (SneakySnake, Table 1 ref. [48]) ------------
+ * Pair p compares read pair_read[p] (read_words: a packed set with base offsets read_off,
+ * n_reads + 1 entries) with window p (win_words: a packed set with base offsets win_off,
+ * n_pairs + 1 entries). Window length must equal the read length + 2 E[p]; E[p] <=
+ * MT_MAX_E, read length <= MT_MAX_READ_LEN. dist[p] = min(obstacles, E[p] + 1).
+ * All pointers are DEVICE pointers. mode: MT_EDA_BATCHED (one persistent work-stealing
+ * launch, autotuned lanes per pair) or MT_EDA_PLAIN (one launch per read-length bucket,
+ * a warp per pair); both give identical dist. The call returns after synchronising
+ * `stream`. Errors: MT_EINVAL (length mismatch, limits), MT_ENOMEM, MT_ECUDA. */
+int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
+                 const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
+                 const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist);
+
+/* ---- continuous-batching serving loop over one resident index --------------------------
+ * Requests (read batches) are admitted while a slot is free and their workspace fits in
+ * hbm_budget bytes; admitted requests run concurrently on their own streams. Inputs are
+ * HOST buffers borrowed until mt_server_poll reports completion. */
+int mt_server_create(const mt_index *ix, uint64_t hbm_budget, int max_slots,
+                     const mt_classify_params *params, mt_server **out);
+int mt_server_submit(mt_server *s, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                     uint64_t n_reads, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                     uint64_t *genome_hits, double *abundance, uint64_t *req_id);
+/* Waits up to timeout_ms (0 = just check) for a request. Returns MT_OK when done (its
+ * outputs are written), MT_EBUSY / MT_ETIMEDOUT while pending, or the request's error.
+ * If latency_s != NULL it receives submit-to-completion seconds. */
+int mt_server_poll(mt_server *s, uint64_t req_id, int timeout_ms, double *latency_s);
+int mt_server_cancel(mt_server *s, uint64_t req_id);
+void mt_server_destroy(mt_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MT_H_ */

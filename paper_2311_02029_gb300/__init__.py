@@ -1,0 +1,327 @@
+"""GB300-native MetaTrinity hot path: Python binding of the C ABI in include/mt.h.
+
+This module only marshals arguments: numpy arrays or torch tensors in, raw pointers and
+sizes to ``libmt.so``, results back as arrays. Every step of the method runs in the CUDA
+kernels of the library; there is no CPU fallback. If the library has not been built, every
+call raises.
+
+    ix = Index(genome_bytes, genome_offsets, k=21, w=11, canonical=1)
+    out = classify(ix, reads, offsets, e_abs=8, min_seeds=3)     # host or CUDA tensors
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmt.so")
+_lib = None
+
+MT_OK, MT_EINVAL, MT_ENOMEM, MT_ETIMEDOUT, MT_ECUDA, MT_ECANCELED, MT_EBUSY = 0, -1, -2, -3, -4, -5, -6
+MT_EDA_BATCHED, MT_EDA_PLAIN = 0, 1
+MAX_READ_LEN, MAX_E, MAX_TOPN = 1024, 127, 8
+
+LOC_DTYPE = np.dtype({"names": ["wstart", "genome", "seeds", "strand", "dist"],
+                      "formats": [np.int64, np.int32, np.uint32, np.uint8, np.uint8],
+                      "offsets": [0, 8, 12, 16, 17], "itemsize": 24})
+
+
+class MtError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = "%s failed: %s (%d)" % (what, _strerror(status), status)
+        if status == MT_ECUDA:
+            msg += ": " + lib().mt_last_cuda_error().decode()
+        super().__init__(msg)
+
+
+class IndexParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("w", ctypes.c_uint32), ("canonical", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class ClassifyParams(ctypes.Structure):
+    _fields_ = [("e_abs", ctypes.c_uint32), ("e_permille", ctypes.c_uint32),
+                ("min_seeds", ctypes.c_uint32), ("top_n", ctypes.c_uint32),
+                ("max_occ", ctypes.c_uint32), ("cont_num", ctypes.c_uint32),
+                ("cont_den", ctypes.c_uint32), ("eda_mode", ctypes.c_uint32),
+                ("abund_cutoff", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("n_reads", "n_minimizers", "n_hits", "n_candidates", "n_accepted", "n_multi",
+                 "n_fallback", "workspace_bytes")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n_genomes", ctypes.c_uint32), ("k", ctypes.c_uint32), ("w", ctypes.c_uint32),
+                ("canonical", ctypes.c_uint32), ("total_bases", ctypes.c_uint64),
+                ("n_occ", ctypes.c_uint64), ("n_keys", ctypes.c_uint64),
+                ("table_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+
+
+EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
+           "mt_index_get_info", "mt_classify", "mt_classify_workspace_bytes", "mt_pack_seqs",
+           "mt_eda_batch", "mt_server_create", "mt_server_submit", "mt_server_poll",
+           "mt_server_cancel", "mt_server_destroy"]
+
+
+def lib():
+    """The loaded CUDA library. Raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmt.so is not built: run __graft_entry__.build() "
+                               "(paper_2311_02029_gb300._build.build()) first")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        L.mt_strerror.restype = ctypes.c_char_p
+        L.mt_strerror.argtypes = [i32]
+        L.mt_last_cuda_error.restype = ctypes.c_char_p
+        L.mt_version.restype = i32
+        L.mt_build_index.restype = i32
+        L.mt_build_index.argtypes = [vp, vp, u32, ctypes.POINTER(IndexParams), vp, ctypes.POINTER(vp)]
+        L.mt_free_index.argtypes = [vp]
+        L.mt_index_get_info.restype = i32
+        L.mt_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
+        L.mt_classify.restype = i32
+        L.mt_classify.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
+                                  vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.mt_classify_workspace_bytes.restype = u64
+        L.mt_classify_workspace_bytes.argtypes = [vp, u64, u64, ctypes.POINTER(ClassifyParams)]
+        L.mt_pack_seqs.restype = i32
+        L.mt_pack_seqs.argtypes = [vp, vp, u64, vp, vp]
+        L.mt_eda_batch.restype = i32
+        L.mt_eda_batch.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp]
+        L.mt_server_create.restype = i32
+        L.mt_server_create.argtypes = [vp, u64, i32, ctypes.POINTER(ClassifyParams), ctypes.POINTER(vp)]
+        L.mt_server_submit.restype = i32
+        L.mt_server_submit.argtypes = [vp, vp, u64, vp, u64, vp, vp, vp, vp, vp, ctypes.POINTER(u64)]
+        L.mt_server_poll.restype = i32
+        L.mt_server_poll.argtypes = [vp, u64, i32, ctypes.POINTER(ctypes.c_double)]
+        L.mt_server_cancel.restype = i32
+        L.mt_server_cancel.argtypes = [vp, u64]
+        L.mt_server_destroy.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _strerror(status: int) -> str:
+    try:
+        return lib().mt_strerror(status).decode()
+    except Exception:  # pragma: no cover
+        return "status %d" % status
+
+
+def _check(rc: int, what: str):
+    if rc != MT_OK:
+        raise MtError(rc, what)
+
+
+# ---- pointer helpers -----------------------------------------------------------------------
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous(), "tensors passed to the library must be contiguous"
+        return ctypes.c_void_p(x.data_ptr())
+    assert isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host_u8(a) -> np.ndarray:
+    if isinstance(a, (bytes, bytearray)):
+        return np.frombuffer(bytes(a), np.uint8)
+    if _is_torch(a):
+        a = a.numpy()
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _host_u64(a) -> np.ndarray:
+    if _is_torch(a):
+        a = a.numpy()
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+# ---- index --------------------------------------------------------------------------------------
+class Index:
+    """Device-resident reference index (``mt_build_index``). Genomes are host bytes."""
+
+    def __init__(self, genomes, offsets, k: int, w: int, canonical: int = 1, stream=None):
+        g = _host_u8(genomes)
+        off = _host_u64(offsets)
+        self.n_genomes = len(off) - 1
+        p = IndexParams(k, w, canonical, 0)
+        h = ctypes.c_void_p()
+        _check(lib().mt_build_index(_ptr(g), _ptr(off), self.n_genomes, ctypes.byref(p),
+                                    _stream(stream), ctypes.byref(h)), "mt_build_index")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = IndexInfo()
+        _check(lib().mt_index_get_info(self._h, ctypes.byref(inf)), "mt_index_get_info")
+        return {n: int(getattr(inf, n)) for n, _ in inf._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mt_free_index(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def classify_params(e_abs=0, e_permille=100, min_seeds=3, top_n=3, max_occ=1024, cont_num=1,
+                    cont_den=10000, eda_mode=MT_EDA_BATCHED, abund_cutoff=1e-4) -> ClassifyParams:
+    return ClassifyParams(e_abs, e_permille, min_seeds, top_n, max_occ, cont_num, cont_den, eda_mode,
+                          abund_cutoff)
+
+
+def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, **params) -> dict:
+    """``mt_classify`` over one read batch. ``reads``/``offsets`` are either host arrays
+    (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors)."""
+    p = classify_params(**params)
+    st = Stats()
+    G = ix.n_genomes
+    if _is_torch(reads) and reads.is_cuda:
+        import torch
+        dev = reads.device
+        n_reads = offsets.numel() - 1
+        out = dict(taxon=torch.empty(n_reads, dtype=torch.int32, device=dev),
+                   nloc=torch.empty(n_reads, dtype=torch.uint8, device=dev),
+                   locs=torch.empty((n_reads, p.top_n, 24), dtype=torch.uint8, device=dev) if want_locs else None,
+                   genome_hits=torch.empty(G, dtype=torch.int64, device=dev),
+                   abundance=torch.empty(G, dtype=torch.float64, device=dev))
+        rc = lib().mt_classify(ix.handle, _ptr(reads), reads.numel(), _ptr(offsets), n_reads, ctypes.byref(p), 1,
+                               _stream(stream), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                               _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+    else:
+        r = _host_u8(reads)
+        off = _host_u64(offsets)
+        n_reads = len(off) - 1
+        out = dict(taxon=np.empty(n_reads, np.int32), nloc=np.empty(n_reads, np.uint8),
+                   locs=np.empty((n_reads, p.top_n), LOC_DTYPE) if want_locs else None,
+                   genome_hits=np.empty(G, np.uint64), abundance=np.empty(G, np.float64))
+        rc = lib().mt_classify(ix.handle, _ptr(r), len(r), _ptr(off), n_reads, ctypes.byref(p), 0,
+                               _stream(stream), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                               _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+    _check(rc, "mt_classify")
+    out["stats"] = st.as_dict()
+    return out
+
+
+def locs_from_device(t) -> np.ndarray:
+    """View a (n, top_n, 24) uint8 tensor of mt_loc records as a structured numpy array."""
+    a = t.cpu().numpy() if _is_torch(t) else t
+    return np.ascontiguousarray(a).view(LOC_DTYPE).reshape(a.shape[0], a.shape[1])
+
+
+def workspace_bytes(ix: Index, n_bases: int, n_reads: int, **params) -> int:
+    p = classify_params(**params)
+    return int(lib().mt_classify_workspace_bytes(ix.handle, n_bases, n_reads, ctypes.byref(p)))
+
+
+# ---- packing and the EDA stage alone -----------------------------------------------------------
+def packed_words(offsets_host: np.ndarray) -> int:
+    n = len(offsets_host) - 1
+    return int(offsets_host[-1]) // 32 + n + 1
+
+
+def pack_seqs(seq, offsets, n_words: int, stream=None):
+    """``mt_pack_seqs``: CUDA uint8 bases + CUDA int64 offsets -> CUDA int64 packed words."""
+    import torch
+    words = torch.empty(n_words, dtype=torch.int64, device=seq.device)
+    _check(lib().mt_pack_seqs(_ptr(seq), _ptr(offsets), offsets.numel() - 1, _ptr(words), _stream(stream)),
+           "mt_pack_seqs")
+    return words
+
+
+def eda_batch(read_words, read_off, win_words, win_off, pair_read, E, mode=MT_EDA_BATCHED, stream=None):
+    """``mt_eda_batch`` on CUDA tensors; returns a CUDA uint8 tensor of distances."""
+    import torch
+    n_pairs = pair_read.numel()
+    dist = torch.empty(n_pairs, dtype=torch.uint8, device=pair_read.device)
+    _check(lib().mt_eda_batch(_ptr(read_words), _ptr(read_off), read_off.numel() - 1, _ptr(win_words),
+                              _ptr(win_off), _ptr(pair_read), _ptr(E), n_pairs, mode, _stream(stream),
+                              _ptr(dist)), "mt_eda_batch")
+    return dist
+
+
+# ---- serving ---------------------------------------------------------------------------------------
+class Server:
+    """Continuous-batching request loop (``mt_server_*``) over one resident index."""
+
+    def __init__(self, ix: Index, hbm_budget: int, max_slots: int = 4, **params):
+        self.ix = ix
+        self.p = classify_params(**params)
+        h = ctypes.c_void_p()
+        _check(lib().mt_server_create(ix.handle, hbm_budget, max_slots, ctypes.byref(self.p), ctypes.byref(h)),
+               "mt_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, reads, offsets) -> int:
+        r = _host_u8(reads)
+        off = _host_u64(offsets)
+        n = len(off) - 1
+        G = self.ix.n_genomes
+        out = dict(taxon=np.empty(n, np.int32), nloc=np.empty(n, np.uint8),
+                   locs=np.empty((n, self.p.top_n), LOC_DTYPE), genome_hits=np.empty(G, np.uint64),
+                   abundance=np.empty(G, np.float64))
+        rid = ctypes.c_uint64()
+        _check(lib().mt_server_submit(self._h, _ptr(r), len(r), _ptr(off), n, _ptr(out["taxon"]),
+                                      _ptr(out["nloc"]), _ptr(out["locs"]), _ptr(out["genome_hits"]),
+                                      _ptr(out["abundance"]), ctypes.byref(rid)), "mt_server_submit")
+        self._keep[rid.value] = (r, off, out)
+        return rid.value
+
+    def poll(self, req_id: int, timeout_ms: int = 0):
+        """(status, latency_s, outputs or None)."""
+        lat = ctypes.c_double(0.0)
+        rc = lib().mt_server_poll(self._h, req_id, timeout_ms, ctypes.byref(lat))
+        if rc in (MT_EBUSY, MT_ETIMEDOUT):
+            return rc, None, None
+        _, _, out = self._keep.pop(req_id)
+        return rc, lat.value, out
+
+    def cancel(self, req_id: int) -> int:
+        return lib().mt_server_cancel(self._h, req_id)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mt_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,969 @@
+// Read classification on the device: the paper's three stages ("The MetaTrinity Pipeline",
+// Fig. 1) over one batch of reads.
+//
+//   k_seed     (stage 1 + 2a-c)  one warp per read: bytes -> 2-bit words in shared memory,
+//              k-mer codes and keys, (w,k)-minimizers by warp-parallel window minima, one
+//              open-addressing probe per minimizer (a 32-byte slot, occurrences inline),
+//              seed matches into shared memory, per-genome containment counts (shared-memory
+//              histogram), warp bitonic sort of the matches by (genome, strand, diagonal),
+//              greedy locations via "next start" pointers, the qualifying locations ranked
+//              and the first C stored. Locations are formed per (genome, strand), so masking
+//              genomes later only removes whole locations: no second seeding pass.
+//   k_mask     (stage 1d)  genome g kept iff hits[g] * den > max(hits) * num.
+//   k_select   (stage 2c)  first top_n stored locations in kept genomes -> candidates.
+//   k_fallback exact slow path, one CTA per read, for reads whose matches overflow shared
+//              memory or whose stored locations run out after masking.
+//   EDA        (stage 2d)  SneakySnake on every candidate (eda.cu).
+//   k_decide   (stage 3a)  per-read decision, unique counts, multi-mapped reads.
+//   k_multi / k_abund (stage 3a-b) multi-read split, relative abundances, 0.01% cutoff.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "eda.cuh"
+#include "internal.h"
+
+namespace mt {
+int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const uint64_t *roff, uint64_t off0,
+                        const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
+                        const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
+                        uint32_t maxn, uint32_t maxE, uint32_t mode, uint8_t *dist,
+                        unsigned long long *counter, cudaStream_t s);
+
+static constexpr unsigned FULL = 0xffffffffu;
+static constexpr int SEED_WARPS = 8;
+static constexpr int SEED_THREADS = SEED_WARPS * 32;
+static constexpr uint32_t TILE = 64;                      // windows per tile
+static constexpr uint32_t KEYS = TILE + MT_MAX_W;         // k-mers a tile may need (<= TILE+w-1)
+static constexpr uint32_t HCAP = 256;                     // seed matches held per read
+static constexpr uint32_t RDW = MT_MAX_READ_LEN / 32 + 2;
+static constexpr uint32_t CSTORE = 8;                     // locations stored per read
+static constexpr uint32_t QOVF = 0xFFFFFFFFu;
+static constexpr uint32_t SMEM_HIST_MAX = 4096;           // genomes counted in shared memory
+static constexpr int FB_CTAS = 16;
+static constexpr int FB_THREADS = 256;
+
+struct WarpSmem {
+    uint64_t rd[RDW];
+    uint64_t key[KEYS];
+    uint64_t code[KEYS];      // code | strand << 63
+    uint64_t mcode[TILE];
+    uint64_t mkey[TILE];
+    uint64_t hits[HCAP];
+    uint16_t mpos[TILE];
+    uint16_t nxt[HCAP];
+    uint16_t qs[HCAP];
+};
+
+enum StatIdx { ST_MINS = 0, ST_HITS, ST_CAND, ST_ACC, ST_MULTI, ST_FB, ST_N };
+
+struct Counters {
+    uint32_t err;
+    uint32_t pad;
+    unsigned long long stat[ST_N];
+    uint64_t cl_count;
+    uint64_t fb_count;
+    uint64_t multi_count;
+    unsigned long long eda_counter;
+    uint32_t maxn;
+    uint32_t pad2;
+};
+
+struct SeedArgs {
+    IndexView ix;
+    const uint8_t *reads;
+    uint64_t n_bases;
+    const uint64_t *roff;
+    uint64_t n_reads;
+    uint64_t off0;
+    int vec_ok;
+    uint32_t e_abs, e_permille, min_seeds, max_occ;
+    uint64_t *rw;
+    uint32_t *qcnt;
+    Cluster *clus;
+    unsigned long long *ghits;
+    uint32_t *fb_list;
+    Counters *ctr;
+};
+
+// ---- read packing (one warp) ------------------------------------------------------------
+MT_DEV bool warp_pack(const uint8_t *reads, uint64_t n_bases, int vec_ok, uint64_t start, uint32_t n,
+                      uint64_t *rd) {
+    const uint32_t lane = lane_id();
+    const uint32_t nw = (n + 31) / 32;
+    for (uint32_t i = lane; i < nw + 2; i += 32) rd[i] = 0;
+    __syncwarp();
+    const uint64_t A = start & ~15ull, end = start + n;
+    const uint32_t nch = (uint32_t)((end - A + 15) >> 4);
+    bool bad = false;
+    for (uint32_t c = lane; c < nch; c += 32) {
+        uint64_t cb = A + 16ull * c;
+        uint32_t by[16];
+        if (vec_ok && cb + 16 <= n_bases) {
+            uint4 v = __ldg(reinterpret_cast<const uint4 *>(reads + cb));
+            uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 16; q++) by[q] = (u[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; q++) by[q] = (cb + q >= start && cb + q < end) ? reads[cb + q] : 'A';
+        }
+        uint32_t c32 = 0;
+#pragma unroll
+        for (int q = 0; q < 16; q++) {
+            uint64_t pos = cb + q;
+            bool in = pos >= start && pos < end;
+            bool b = false;
+            uint32_t code = base_code(by[q], b);
+            if (in) { bad |= b; c32 |= code << (2 * q); }
+        }
+        int64_t j0 = (int64_t)cb - (int64_t)start;
+        if (j0 < 0) { c32 >>= (uint32_t)(2 * (-j0)); j0 = 0; }
+        uint32_t wi = (uint32_t)(j0 >> 5), o = (uint32_t)(2 * (j0 & 31));
+        atomicOr(reinterpret_cast<unsigned long long *>(&rd[wi]), (unsigned long long)c32 << o);
+        if (o > 32) atomicOr(reinterpret_cast<unsigned long long *>(&rd[wi + 1]), (unsigned long long)c32 >> (64 - o));
+    }
+    __syncwarp();
+    return __any_sync(FULL, bad);
+}
+
+MT_DEV uint32_t lower_bound_u64(const uint64_t *a, uint32_t lo, uint32_t hi, uint64_t key) {
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// warp bitonic sort of a[0, P), P a power of two >= 2
+MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
+    const uint32_t lane = lane_id();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = lane; i < P / 2; i += 32) {
+                uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                uint32_t hi = lo + j;
+                bool up = (lo & k) == 0;
+                uint64_t x = a[lo], y = a[hi];
+                if ((x > y) == up) { a[lo] = y; a[hi] = x; }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <bool SMEM_HIST>
+__global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smraw);
+    const uint32_t hist_n = SMEM_HIST ? A.ix.G : 0;
+    WarpSmem *wsall = reinterpret_cast<WarpSmem *>(smraw + ((hist_n * 8 + 15) & ~15u));
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    WarpSmem &ws = wsall[warp];
+    if (SMEM_HIST) {
+        for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x) hist[g] = 0;
+        __syncthreads();
+    }
+    unsigned long long *H_out = SMEM_HIST ? hist : A.ghits;
+    const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
+    unsigned long long n_mins = 0, n_hits = 0;
+
+    const uint64_t total_warps = (uint64_t)gridDim.x * SEED_WARPS;
+    for (uint64_t r = (uint64_t)blockIdx.x * SEED_WARPS + warp; r < A.n_reads; r += total_warps) {
+        const uint64_t start = A.roff[r], end = A.roff[r + 1];
+        if (end < start || end > A.n_bases) {
+            if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_OFFSETS); A.qcnt[r] = 0; }
+            continue;
+        }
+        const uint64_t n64 = end - start;
+        if (n64 > MT_MAX_READ_LEN) {
+            if (lane == 0) { atomicOr(&A.ctr->err, ERR_READ_TOO_LONG); A.qcnt[r] = 0; }
+            continue;
+        }
+        const uint32_t n = (uint32_t)n64;
+        if (warp_pack(A.reads, A.n_bases, A.vec_ok, start, n, ws.rd)) {
+            if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_BASE); A.qcnt[r] = 0; }
+            continue;
+        }
+        {   // packed read for the approximation stage
+            uint64_t *dst = A.rw + seq_word(start, A.off0, r);
+            for (uint32_t t = lane; t < (n + 31) / 32; t += 32) dst[t] = ws.rd[t];
+        }
+        const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
+        if (n < k || n - k + 1 < w) {
+            if (lane == 0) A.qcnt[r] = 0;
+            continue;
+        }
+        const uint32_t nwin = n - k - w + 2;
+        uint32_t H = 0;
+        bool ovf = false;
+        int32_t carry = -1;
+        for (uint32_t t0 = 0; t0 < nwin; t0 += TILE) {
+            const uint32_t tw = min(TILE, nwin - t0);
+            const uint32_t npos = tw + w - 1;
+            for (uint32_t i = lane; i < npos; i += 32) {
+                uint64_t x = get32(ws.rd, t0 + i);
+                uint64_t fwd, rc, c;
+                uint32_t st;
+                kmer_codes(x, k, fwd, rc);
+                canon(fwd, rc, canonical, c, st);
+                ws.key[i] = mix64(c);
+                ws.code[i] = c | ((uint64_t)st << 63);
+            }
+            __syncwarp();
+            uint32_t nm = 0;
+            for (uint32_t rr = 0; rr * 32 < tw; rr++) {
+                uint32_t j = rr * 32 + lane;
+                int32_t sel = -1;
+                if (j < tw) {
+                    uint32_t b = j;
+                    uint64_t bk = ws.key[j];
+                    for (uint32_t t = 1; t < w; t++) {
+                        uint64_t kk = ws.key[j + t];
+                        if (kk < bk) { bk = kk; b = j + t; }
+                    }
+                    sel = (int32_t)(t0 + b);
+                }
+                int32_t prv = __shfl_up_sync(FULL, sel, 1);
+                if (lane == 0) prv = carry;
+                bool emit = (j < tw) && (sel != prv);
+                unsigned bal = __ballot_sync(FULL, emit);
+                if (emit) {
+                    uint32_t slot = nm + __popc(bal & ((1u << lane) - 1u));
+                    uint32_t li = (uint32_t)sel - t0;
+                    ws.mcode[slot] = ws.code[li];
+                    ws.mkey[slot] = ws.key[li];
+                    ws.mpos[slot] = (uint16_t)sel;
+                }
+                nm += __popc(bal);
+                uint32_t last = min(31u, tw - 1 - rr * 32);
+                carry = __shfl_sync(FULL, sel, last);
+            }
+            __syncwarp();
+            n_mins += nm;
+            for (uint32_t m0 = 0; m0 < nm; m0 += 32) {
+                const uint32_t m = m0 + lane;
+                Lookup L;
+                L.cnt = 0; L.ninline = 0; L.off = 0;
+                uint32_t cnt = 0, rpos = 0, rst = 0;
+                if (m < nm) {
+                    uint64_t cs = ws.mcode[m];
+                    rst = (uint32_t)(cs >> 63);
+                    rpos = ws.mpos[m];
+                    L = probe(A.ix, cs & CODE_MASK62, ws.mkey[m], &A.ctr->err);
+                    cnt = L.cnt <= A.max_occ ? L.cnt : 0;
+                }
+                uint32_t incl = warp_incl_scan(cnt);
+                uint32_t total = __shfl_sync(FULL, incl, 31);
+                uint32_t excl = incl - cnt;
+                if (!ovf && H + total > HCAP) {
+                    // switch to counting only: count what is buffered so far
+                    for (uint32_t i = lane; i < H; i += 32) atomicAdd(&H_out[hk_genome(ws.hits[i])], 1ull);
+                    ovf = true;
+                }
+                if (!ovf) {
+                    for (uint32_t t = 0; t < cnt; t++)
+                        ws.hits[H + excl + t] = hit_key(occ_at(A.ix, L, t), rpos, rst, n, k);
+                } else {
+                    for (uint32_t t = 0; t < cnt; t++) atomicAdd(&H_out[occ_at(A.ix, L, t) >> 33], 1ull);
+                }
+                H += total;
+            }
+            __syncwarp();
+        }
+        n_hits += H;
+        if (ovf) {
+            if (lane == 0) {
+                A.qcnt[r] = QOVF;
+                unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctr->fb_count), 1ull);
+                A.fb_list[slot] = (uint32_t)r;
+            }
+            continue;
+        }
+        if (H == 0) {
+            if (lane == 0) A.qcnt[r] = 0;
+            continue;
+        }
+        uint32_t P = 2;
+        while (P < H) P <<= 1;
+        for (uint32_t i = H + lane; i < P; i += 32) ws.hits[i] = ~0ull;
+        __syncwarp();
+        warp_bitonic(ws.hits, P);
+        // containment counts, one atomic per genome run
+        for (uint32_t i = lane; i < H; i += 32) {
+            uint32_t g = hk_genome(ws.hits[i]);
+            if (i == 0 || hk_genome(ws.hits[i - 1]) != g) {
+                uint32_t e = lower_bound_u64(ws.hits, i + 1, H, ((uint64_t)g + 1) << 34);
+                atomicAdd(&H_out[g], (unsigned long long)(e - i));
+            }
+        }
+        // greedy locations: a location starting at match i ends before the first match
+        // with key >= key_i + E + 1 (a later diagonal band, strand or genome)
+        for (uint32_t i = lane; i < H; i += 32)
+            ws.nxt[i] = (uint16_t)lower_bound_u64(ws.hits, i + 1, H, ws.hits[i] + E + 1);
+        __syncwarp();
+        uint32_t Q = 0;
+        if (lane == 0) {
+            uint32_t s = 0;
+            while (s < H) {
+                uint32_t e = ws.nxt[s];
+                if (e - s >= A.min_seeds) ws.qs[Q++] = (uint16_t)s;
+                s = e;
+            }
+        }
+        Q = __shfl_sync(FULL, Q, 0);
+        __syncwarp();
+        for (uint32_t qi = lane; qi < Q; qi += 32) {
+            uint32_t si = ws.qs[qi];
+            uint32_t seeds_i = ws.nxt[si] - si;
+            uint64_t hk_i = ws.hits[si];
+            uint32_t rank = 0;
+            for (uint32_t qj = 0; qj < Q; qj++) {
+                uint32_t sj = ws.qs[qj];
+                uint32_t seeds_j = ws.nxt[sj] - sj;
+                uint64_t hk_j = ws.hits[sj];
+                rank += (seeds_j > seeds_i) || (seeds_j == seeds_i && hk_j < hk_i);
+            }
+            if (rank < CSTORE) {
+                Cluster c;
+                c.hkey = hk_i; c.seeds = seeds_i; c.pad = 0;
+                A.clus[r * CSTORE + rank] = c;
+            }
+        }
+        if (lane == 0) A.qcnt[r] = Q;
+        __syncwarp();
+    }
+    if (lane == 0) {
+        atomicAdd(&A.ctr->stat[ST_MINS], n_mins);
+        atomicAdd(&A.ctr->stat[ST_HITS], n_hits);
+    }
+    if (SMEM_HIST) {
+        __syncthreads();
+        for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x)
+            if (hist[g]) atomicAdd(&A.ghits[g], hist[g]);
+    }
+}
+
+// ---- containment mask ----------------------------------------------------------------------
+__global__ void k_mask(const unsigned long long *hits, uint32_t G, uint32_t num, uint32_t den, uint8_t *keep) {
+    __shared__ unsigned long long smax[32];
+    unsigned long long m = 0;
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) m = max(m, hits[g]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x + 31) / 32 ? smax[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(FULL, m, o));
+        if (threadIdx.x == 0) smax[0] = m;
+    }
+    __syncthreads();
+    const unsigned long long mx = smax[0];
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) {
+        unsigned long long h = hits[g];
+        // compare h * den > mx * num exactly in 128 bits
+        unsigned long long lo1 = h * den, hi1 = __umul64hi(h, den);
+        unsigned long long lo2 = mx * num, hi2 = __umul64hi(mx, num);
+        bool gt = (hi1 > hi2) || (hi1 == hi2 && lo1 > lo2);
+        keep[g] = (mx > 0 && gt) ? 1 : 0;
+    }
+}
+
+// ---- candidate selection ----------------------------------------------------------------------
+__global__ void k_select(uint64_t n_reads, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep,
+                         uint32_t top_n, Cluster *cand, uint8_t *nloc_ws, uint32_t *cl, uint32_t *fb_list,
+                         Counters *ctr) {
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t r = r0 + threadIdx.x;
+        uint32_t taken = 0;
+        bool fb = false;
+        if (r < n_reads) {
+            uint32_t q = qcnt[r];
+            if (q == QOVF) {
+                fb = false;   // queued by the seeding pass
+                nloc_ws[r] = 0;
+            } else {
+                uint32_t lim = min(q, CSTORE);
+                for (uint32_t i = 0; i < lim && taken < top_n; i++) {
+                    Cluster c = clus[r * CSTORE + i];
+                    if (keep[hk_genome(c.hkey)]) cand[r * top_n + taken++] = c;
+                }
+                if (taken < top_n && q > CSTORE) { fb = true; taken = 0; }
+                nloc_ws[r] = (uint8_t)taken;
+            }
+        }
+        if (fb) {
+            unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->fb_count), 1ull);
+            fb_list[slot] = (uint32_t)r;
+        }
+        // compact candidate slots
+        uint32_t incl = warp_incl_scan(taken);
+        uint32_t tot = __shfl_sync(FULL, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 31 && tot) base = atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->cl_count), (unsigned long long)tot);
+        base = __shfl_sync(FULL, base, 31);
+        for (uint32_t t = 0; t < taken; t++) cl[base + incl - taken + t] = (uint32_t)(r * top_n + t);
+    }
+}
+
+// ---- exact slow path -------------------------------------------------------------------------------
+struct FbArgs {
+    IndexView ix;
+    const uint64_t *rw, *roff;
+    uint64_t off0;
+    uint32_t e_abs, e_permille, min_seeds, max_occ, top_n;
+    const uint8_t *keep;
+    const uint32_t *fb_list;
+    Cluster *cand;
+    uint8_t *nloc_ws;
+    uint32_t *cl;
+    Counters *ctr;
+    uint64_t *scratch;     // FB_CTAS * cap hit keys, then FB_CTAS * cap u32 next pointers
+    uint64_t cap;          // power of two
+};
+
+MT_DEV void read_kmer(const uint64_t *rd, uint32_t p, uint32_t k, uint32_t canonical, uint64_t &code,
+                      uint32_t &st, uint64_t &key) {
+    uint64_t fwd, rc;
+    kmer_codes(get32(rd, p), k, fwd, rc);
+    canon(fwd, rc, canonical, code, st);
+    key = mix64(code);
+}
+
+MT_DEV uint32_t window_sel(const uint64_t *rd, uint32_t j, uint32_t k, uint32_t w, uint32_t canonical) {
+    uint64_t c, kk, bk;
+    uint32_t st, b = j;
+    read_kmer(rd, j, k, canonical, c, st, bk);
+    for (uint32_t t = j + 1; t < j + w; t++) {
+        read_kmer(rd, t, k, canonical, c, st, kk);
+        if (kk < bk) { bk = kk; b = t; }
+    }
+    return b;
+}
+
+__global__ void __launch_bounds__(FB_THREADS) k_fallback(FbArgs A) {
+    __shared__ unsigned long long s_H;
+    __shared__ uint32_t s_best_start[MT_MAX_TOPN], s_best_seeds[MT_MAX_TOPN];
+    __shared__ uint32_t s_nbest;
+    uint64_t *hits = A.scratch + (uint64_t)blockIdx.x * A.cap;
+    uint32_t *nxt = reinterpret_cast<uint32_t *>(A.scratch + (uint64_t)FB_CTAS * A.cap) + (uint64_t)blockIdx.x * A.cap;
+    const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
+    for (uint64_t fi = blockIdx.x; fi < A.ctr->fb_count; fi += gridDim.x) {
+        const uint32_t r = A.fb_list[fi];
+        const uint64_t start = A.roff[r];
+        const uint32_t n = (uint32_t)(A.roff[r + 1] - start);
+        const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
+        const uint64_t *rd = A.rw + seq_word(start, A.off0, r);
+        if (threadIdx.x == 0) s_H = 0;
+        __syncthreads();
+        const uint32_t nwin = n - k - w + 2;   // the read reached here, so it has windows
+        for (uint32_t j = threadIdx.x; j < nwin; j += blockDim.x) {
+            uint32_t sel = window_sel(rd, j, k, w, canonical);
+            if (j > 0 && window_sel(rd, j - 1, k, w, canonical) == sel) continue;
+            uint64_t code, key;
+            uint32_t st;
+            read_kmer(rd, sel, k, canonical, code, st, key);
+            Lookup L = probe(A.ix, code, key, &A.ctr->err);
+            if (L.cnt > A.max_occ) continue;
+            for (uint32_t t = 0; t < L.cnt; t++) {
+                uint64_t o = occ_at(A.ix, L, t);
+                if (!A.keep[o >> 33]) continue;
+                unsigned long long pos = atomicAdd(&s_H, 1ull);
+                if (pos < A.cap) hits[pos] = hit_key(o, sel, st, n, k);
+                else atomicOr(&A.ctr->err, ERR_SCRATCH);
+            }
+        }
+        __syncthreads();
+        const uint32_t H = (uint32_t)umin64(s_H, A.cap);
+        uint32_t P = 2;
+        while (P < H) P <<= 1;
+        for (uint32_t i = H + threadIdx.x; i < P; i += blockDim.x) hits[i] = ~0ull;
+        __syncthreads();
+        for (uint32_t kk = 2; kk <= P; kk <<= 1) {
+            for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                    uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                    uint32_t hi = lo + j;
+                    bool up = (lo & kk) == 0;
+                    uint64_t x = hits[lo], y = hits[hi];
+                    if ((x > y) == up) { hits[lo] = y; hits[hi] = x; }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
+            uint64_t key = hits[i] + E + 1;
+            uint32_t lo = i + 1, hi = H;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (hits[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            nxt[i] = lo;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // walk the locations; keep the top_n by (seeds desc, key asc) in a small list
+            uint32_t nb = 0;
+            uint32_t s = 0;
+            while (s < H) {
+                uint32_t e = nxt[s];
+                uint32_t seeds = e - s;
+                if (seeds >= A.min_seeds) {
+                    uint32_t pos = nb;
+                    while (pos > 0) {
+                        uint32_t ps = s_best_seeds[pos - 1];
+                        bool before = ps > seeds || (ps == seeds && hits[s_best_start[pos - 1]] < hits[s]);
+                        if (before) break;
+                        pos--;
+                    }
+                    if (pos < A.top_n) {
+                        uint32_t last = min(nb, A.top_n - 1);
+                        for (uint32_t q = last; q > pos; q--) {
+                            s_best_seeds[q] = s_best_seeds[q - 1];
+                            s_best_start[q] = s_best_start[q - 1];
+                        }
+                        s_best_seeds[pos] = seeds;
+                        s_best_start[pos] = s;
+                        if (nb < A.top_n) nb++;
+                    }
+                }
+                s = e;
+            }
+            s_nbest = nb;
+            unsigned long long base = nb ? atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctr->cl_count), (unsigned long long)nb) : 0;
+            for (uint32_t q = 0; q < nb; q++) {
+                Cluster c;
+                c.hkey = hits[s_best_start[q]];
+                c.seeds = s_best_seeds[q];
+                c.pad = 0;
+                A.cand[(uint64_t)r * A.top_n + q] = c;
+                A.cl[base + q] = r * A.top_n + q;
+            }
+            A.nloc_ws[r] = (uint8_t)nb;
+            atomicAdd(&A.ctr->stat[ST_FB], 1ull);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- per-read decision -------------------------------------------------------------------------------
+struct DecideArgs {
+    uint64_t n_reads;
+    const uint64_t *roff;
+    uint32_t e_abs, e_permille, top_n;
+    const uint8_t *nloc_ws;
+    const Cluster *cand;
+    const uint8_t *dist;
+    int32_t *taxon;
+    uint8_t *nloc;
+    mt_loc *locs;
+    unsigned long long *U;
+    int32_t *multi_set;
+    uint32_t *multi_list;
+    Counters *ctr;
+};
+
+__global__ void k_decide(DecideArgs A) {
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned long long acc = 0, mul = 0, cand = 0;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < A.n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = r0 + threadIdx.x;
+        int32_t uniq = -1;
+        bool is_multi = false;
+        if (r < A.n_reads) {
+            uint32_t n = (uint32_t)(A.roff[r + 1] - A.roff[r]);
+            uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
+            uint32_t nl = A.nloc_ws[r];
+            cand += nl;
+            uint32_t best = E + 1;
+            for (uint32_t t = 0; t < nl; t++) {
+                uint32_t d = A.dist[r * A.top_n + t];
+                if (d <= E && d < best) best = d;
+            }
+            int32_t tax = -1;
+            int32_t S[MT_MAX_TOPN];
+            uint32_t ns = 0;
+            for (uint32_t t = 0; t < A.top_n; t++) {
+                mt_loc L;
+                memset(&L, 0, sizeof(L));
+                L.genome = -1;
+                if (t < nl) {
+                    Cluster c = A.cand[r * A.top_n + t];
+                    uint32_t d = A.dist[r * A.top_n + t];
+                    int32_t g = (int32_t)hk_genome(c.hkey);
+                    L.wstart = hk_diag(c.hkey) - (int64_t)E;
+                    L.genome = g;
+                    L.seeds = c.seeds;
+                    L.strand = (uint8_t)hk_rel(c.hkey);
+                    L.dist = (uint8_t)d;
+                    if (best <= E && d == best) {
+                        if (tax < 0) tax = g;
+                        bool seen = false;
+                        for (uint32_t q = 0; q < ns; q++) seen |= (S[q] == g);
+                        if (!seen) S[ns++] = g;
+                    }
+                }
+                if (A.locs) A.locs[r * A.top_n + t] = L;
+            }
+            A.taxon[r] = tax;
+            if (A.nloc) A.nloc[r] = (uint8_t)nl;
+            if (ns == 1) uniq = S[0];
+            if (ns >= 2) {
+                is_multi = true;
+                for (uint32_t q = 0; q < A.top_n; q++) A.multi_set[r * A.top_n + q] = q < ns ? S[q] : -1;
+            }
+            acc += (best <= E);
+            mul += is_multi;
+        }
+        // unique counts, aggregated over lanes hitting the same genome
+        unsigned act = __ballot_sync(FULL, uniq >= 0);
+        if (uniq >= 0) {
+            unsigned peers = __match_any_sync(act, uniq);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&A.U[uniq], (unsigned long long)__popc(peers));
+        }
+        unsigned mb = __ballot_sync(FULL, is_multi);
+        unsigned long long base = 0;
+        if (lane == 0 && mb) base = atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctr->multi_count), (unsigned long long)__popc(mb));
+        base = __shfl_sync(FULL, base, 0);
+        if (is_multi) A.multi_list[base + __popc(mb & ((1u << lane) - 1u))] = (uint32_t)r;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(FULL, acc, o);
+        mul += __shfl_xor_sync(FULL, mul, o);
+        cand += __shfl_xor_sync(FULL, cand, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.ctr->stat[ST_ACC], acc);
+        atomicAdd(&A.ctr->stat[ST_MULTI], mul);
+        atomicAdd(&A.ctr->stat[ST_CAND], cand);
+    }
+}
+
+// multi-mapped reads: split by the genomes' unique counts (equally when they have none)
+__global__ void k_multi(const uint32_t *multi_list, const Counters *ctr, const int32_t *multi_set, uint32_t top_n,
+                        const unsigned long long *U, double *M) {
+    const uint64_t cnt = ctr->multi_count;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = multi_list[i];
+        const int32_t *S = multi_set + (uint64_t)r * top_n;
+        uint32_t ns = 0;
+        unsigned long long tot = 0;
+        while (ns < top_n && S[ns] >= 0) { tot += U[S[ns]]; ns++; }
+        for (uint32_t q = 0; q < ns; q++)
+            atomicAdd(&M[S[q]], tot ? (double)U[S[q]] / (double)tot : 1.0 / (double)ns);
+    }
+}
+
+MT_DEV double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x == 0) {
+        for (uint32_t i = 0; i < (blockDim.x + 31) / 32; i++) t += sh[i];
+        sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// relative abundances: a = (U + M) / sum; entries below the cutoff dropped; renormalised.
+// One block; per-thread partial sums in a fixed order, so the result is deterministic for
+// a given U and M.
+__global__ void k_abund(uint32_t G, const unsigned long long *U, const double *M, double cutoff, double *out) {
+    __shared__ double sh[33];
+    double part = 0;
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) part += (double)U[g] + M[g];
+    double sum = block_sum(part, sh);
+    double part2 = 0;
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) {
+        double a = sum > 0 ? ((double)U[g] + M[g]) / sum : 0.0;
+        if (a < cutoff) a = 0.0;
+        out[g] = a;
+        part2 += a;
+    }
+    double kept = block_sum(part2, sh);
+    if (kept > 0)
+        for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) out[g] /= kept;
+}
+
+// longest read and offset sanity for device-resident inputs
+__global__ void k_maxlen(const uint64_t *roff, uint64_t n_reads, uint64_t n_bases, Counters *ctr) {
+    unsigned int mx = 0;
+    bool bad = false;
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_reads; r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t a = roff[r], b = roff[r + 1];
+        if (b < a || b > n_bases) { bad = true; continue; }
+        uint64_t n = b - a;
+        mx = max(mx, (unsigned int)umin64(n, 0xFFFFFFFFull));
+    }
+    atomicMax(&ctr->maxn, mx);
+    if (bad) atomicOr(&ctr->err, ERR_BAD_OFFSETS);
+}
+
+}  // namespace mt
+
+using namespace mt;
+
+// ---- host orchestration ---------------------------------------------------------------------------------
+namespace {
+
+struct Layout {
+    size_t rw, qcnt, clus, keep, ghits, cand, nloc_ws, cl, dist, fb_list, multi_list, multi_set, U, M, abund,
+        ctr, fb_scratch, taxon, nloc, locs, reads, roff, total;
+    uint64_t rw_words, fb_cap;
+};
+
+uint64_t fb_cap_for(uint32_t maxn, uint32_t k, uint32_t w, uint32_t max_occ) {
+    uint64_t nmin = (maxn >= k + w - 1) ? (uint64_t)(maxn - k - w + 2) : 1;
+    uint64_t need = nmin * std::max<uint32_t>(max_occ, 1);
+    uint64_t cap = 2;
+    while (cap < need) cap <<= 1;
+    return cap;
+}
+
+Layout plan_layout(const mt_index *ix, uint64_t n_bases, uint64_t n_reads, uint32_t top_n, uint32_t maxn,
+                   uint32_t max_occ, bool host_io) {
+    Layout L{};
+    Carver c;
+    L.rw_words = (n_bases >> 5) + n_reads + 2;
+    L.rw = c.take<uint64_t>(L.rw_words);
+    L.qcnt = c.take<uint32_t>(n_reads);
+    L.clus = c.take<Cluster>(n_reads * CSTORE);
+    L.keep = c.take<uint8_t>(ix->G);
+    L.ghits = c.take<uint64_t>(ix->G);
+    L.cand = c.take<Cluster>(n_reads * top_n);
+    L.nloc_ws = c.take<uint8_t>(n_reads);
+    L.cl = c.take<uint32_t>(n_reads * top_n);
+    L.dist = c.take<uint8_t>(n_reads * top_n);
+    L.fb_list = c.take<uint32_t>(n_reads);
+    L.multi_list = c.take<uint32_t>(n_reads);
+    L.multi_set = c.take<int32_t>(n_reads * top_n);
+    L.U = c.take<uint64_t>(ix->G);
+    L.M = c.take<double>(ix->G);
+    L.abund = c.take<double>(ix->G);
+    L.ctr = c.take<Counters>(1);
+    L.fb_cap = fb_cap_for(maxn, ix->k, ix->w, max_occ);
+    L.fb_scratch = c.take<uint8_t>((uint64_t)FB_CTAS * L.fb_cap * 12);
+    if (host_io) {
+        L.taxon = c.take<int32_t>(n_reads);
+        L.nloc = c.take<uint8_t>(n_reads);
+        L.locs = c.take<mt_loc>(n_reads * top_n);
+        L.reads = c.take<uint8_t>(n_bases + 16);
+        L.roff = c.take<uint64_t>(n_reads + 1);
+    }
+    L.total = c.off + 256;
+    return L;
+}
+
+int check_params(const mt_classify_params *p) {
+    if (!p) return MT_EINVAL;
+    if (p->top_n < 1 || p->top_n > MT_MAX_TOPN) return MT_EINVAL;
+    if (p->min_seeds < 1) return MT_EINVAL;
+    if (p->max_occ > MT_MAX_OCC_LIMIT) return MT_EINVAL;
+    if (p->cont_den == 0) return MT_EINVAL;
+    if (p->eda_mode != MT_EDA_BATCHED && p->eda_mode != MT_EDA_PLAIN) return MT_EINVAL;
+    if (p->e_permille > 1000) return MT_EINVAL;
+    if (p->e_permille == 0 && p->e_abs > MT_MAX_E) return MT_EINVAL;
+    if (!(p->abund_cutoff >= 0.0)) return MT_EINVAL;
+    return MT_OK;
+}
+
+}  // namespace
+
+uint64_t mt::classify_ws_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
+                               const mt_classify_params *p, uint32_t maxn, bool host_io) {
+    if (!ix || !p || check_params(p)) return 0;
+    return plan_layout(ix, n_bases, n_reads, p->top_n, std::max<uint32_t>(maxn, 1), p->max_occ, host_io).total;
+}
+
+extern "C" uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
+                                                const mt_classify_params *p) {
+    if (!ix || !p || check_params(p)) return 0;
+    uint32_t maxn = (uint32_t)std::min<uint64_t>(n_bases, MT_MAX_READ_LEN);
+    return plan_layout(ix, n_bases, n_reads, p->top_n, maxn, p->max_occ, false).total;
+}
+
+extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                           uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
+                           int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
+                           mt_stats *stats) {
+    if (!ix || !offsets || !taxon || (!reads && n_bases)) return MT_EINVAL;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (n_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t G = ix->G, top_n = p->top_n;
+    const bool host_io = !device_ptrs;
+    if (stats) memset(stats, 0, sizeof(*stats));
+
+    // longest read and offset checks
+    uint32_t maxn = 0;
+    uint64_t off0 = 0;
+    Counters *pre = nullptr;
+    if (host_io) {
+        if (n_reads) off0 = offsets[0];
+        for (uint64_t r = 0; r < n_reads; r++) {
+            if (offsets[r + 1] < offsets[r] || offsets[r + 1] > n_bases) return MT_EINVAL;
+            maxn = (uint32_t)std::max<uint64_t>(maxn, std::min<uint64_t>(offsets[r + 1] - offsets[r], 0xFFFFFFFFull));
+        }
+    } else if (n_reads) {
+        if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) return rc;
+        MT_CK(cudaMemsetAsync(pre, 0, sizeof(Counters), s));
+        unsigned blocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 4);
+        k_maxlen<<<blocks, 256, 0, s>>>(offsets, n_reads, n_bases, pre);
+        MT_CK(cudaGetLastError());
+        Counters h{};
+        MT_CK(cudaMemcpyAsync(&h, pre, sizeof(h), cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaStreamSynchronize(s));
+        dfree(pre, s);
+        if (h.err) return MT_EINVAL;
+        maxn = h.maxn;
+    }
+    if (maxn > MT_MAX_READ_LEN) return MT_EINVAL;
+    const uint32_t maxE = edit_threshold(maxn, p->e_abs, p->e_permille);
+    if (maxE > MT_MAX_E) return MT_EINVAL;
+
+    Layout L = plan_layout(ix, n_bases, n_reads, top_n, std::max<uint32_t>(maxn, 1), p->max_occ, host_io);
+    unsigned char *ws = nullptr;
+    if ((rc = dalloc((void **)&ws, L.total, s))) return rc;
+    auto P = [&](size_t off) { return (void *)(ws + off); };
+    const uint8_t *d_reads = reads;
+    const uint64_t *d_roff = offsets;
+    int32_t *d_taxon = taxon;
+    uint8_t *d_nloc = nloc;
+    mt_loc *d_locs = locs;
+    if (host_io) {
+        d_reads = (const uint8_t *)P(L.reads);
+        d_roff = (const uint64_t *)P(L.roff);
+        d_taxon = (int32_t *)P(L.taxon);
+        d_nloc = (uint8_t *)P(L.nloc);
+        d_locs = locs ? (mt_loc *)P(L.locs) : nullptr;
+        if (n_bases) MT_CK(cudaMemcpyAsync((void *)d_reads, reads, n_bases, cudaMemcpyHostToDevice, s));
+        MT_CK(cudaMemcpyAsync((void *)d_roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+    }
+    Counters *ctr = (Counters *)P(L.ctr);
+    unsigned long long *ghits = (unsigned long long *)P(L.ghits);
+    unsigned long long *U = (unsigned long long *)P(L.U);
+    double *M = (double *)P(L.M);
+    MT_CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+    MT_CK(cudaMemsetAsync(ghits, 0, G * 8, s));
+    MT_CK(cudaMemsetAsync(U, 0, G * 8, s));
+    MT_CK(cudaMemsetAsync(M, 0, G * 8, s));
+
+    IndexView iv = ix->view();
+    if (n_reads) {
+        SeedArgs A;
+        A.ix = iv;
+        A.reads = d_reads;
+        A.n_bases = n_bases;
+        A.roff = d_roff;
+        A.n_reads = n_reads;
+        A.off0 = off0;
+        A.vec_ok = ((uintptr_t)d_reads & 15u) == 0;
+        A.e_abs = p->e_abs; A.e_permille = p->e_permille; A.min_seeds = p->min_seeds; A.max_occ = p->max_occ;
+        A.rw = (uint64_t *)P(L.rw);
+        A.qcnt = (uint32_t *)P(L.qcnt);
+        A.clus = (Cluster *)P(L.clus);
+        A.ghits = ghits;
+        A.fb_list = (uint32_t *)P(L.fb_list);
+        A.ctr = ctr;
+        bool smem_hist = G <= SMEM_HIST_MAX;
+        size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem);
+        int per_sm = 0;
+        if (smem_hist) {
+            MT_CK(cudaFuncSetAttribute(k_seed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<true>, SEED_THREADS, smem));
+        } else {
+            MT_CK(cudaFuncSetAttribute(k_seed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<false>, SEED_THREADS, smem));
+        }
+        per_sm = std::max(per_sm, 1);
+        uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
+        unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
+        if (smem_hist) k_seed<true><<<grid, SEED_THREADS, smem, s>>>(A);
+        else k_seed<false><<<grid, SEED_THREADS, smem, s>>>(A);
+        MT_CK(cudaGetLastError());
+
+        k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
+        MT_CK(cudaGetLastError());
+
+        unsigned rblocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 8);
+        k_select<<<rblocks, 256, 0, s>>>(n_reads, A.qcnt, A.clus, (const uint8_t *)P(L.keep), top_n,
+                                         (Cluster *)P(L.cand), (uint8_t *)P(L.nloc_ws), (uint32_t *)P(L.cl),
+                                         A.fb_list, ctr);
+        MT_CK(cudaGetLastError());
+
+        FbArgs F;
+        F.ix = iv;
+        F.rw = A.rw; F.roff = d_roff; F.off0 = off0;
+        F.e_abs = p->e_abs; F.e_permille = p->e_permille; F.min_seeds = p->min_seeds; F.max_occ = p->max_occ;
+        F.top_n = top_n;
+        F.keep = (const uint8_t *)P(L.keep);
+        F.fb_list = A.fb_list;
+        F.cand = (Cluster *)P(L.cand);
+        F.nloc_ws = (uint8_t *)P(L.nloc_ws);
+        F.cl = (uint32_t *)P(L.cl);
+        F.ctr = ctr;
+        F.scratch = (uint64_t *)P(L.fb_scratch);
+        F.cap = L.fb_cap;
+        k_fallback<<<FB_CTAS, FB_THREADS, 0, s>>>(F);
+        MT_CK(cudaGetLastError());
+
+        rc = launch_classify_eda(iv, A.rw, d_roff, off0, (const uint32_t *)P(L.cl), &ctr->cl_count,
+                                 n_reads * top_n, (const Cluster *)P(L.cand), top_n, p->e_abs, p->e_permille,
+                                 std::max<uint32_t>(maxn, 1), maxE, p->eda_mode, (uint8_t *)P(L.dist),
+                                 &ctr->eda_counter, s);
+        if (rc) { dfree(ws, s); return rc; }
+
+        DecideArgs D;
+        D.n_reads = n_reads; D.roff = d_roff;
+        D.e_abs = p->e_abs; D.e_permille = p->e_permille; D.top_n = top_n;
+        D.nloc_ws = (const uint8_t *)P(L.nloc_ws);
+        D.cand = (const Cluster *)P(L.cand);
+        D.dist = (const uint8_t *)P(L.dist);
+        D.taxon = d_taxon; D.nloc = d_nloc; D.locs = d_locs;
+        D.U = U;
+        D.multi_set = (int32_t *)P(L.multi_set);
+        D.multi_list = (uint32_t *)P(L.multi_list);
+        D.ctr = ctr;
+        k_decide<<<rblocks, 256, 0, s>>>(D);
+        MT_CK(cudaGetLastError());
+        k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(D.multi_list, ctr, D.multi_set, top_n, U, M);
+        MT_CK(cudaGetLastError());
+    }
+    double *d_ab = (double *)P(L.abund);
+    k_abund<<<1, 1024, 0, s>>>(G, U, M, p->abund_cutoff, d_ab);
+    MT_CK(cudaGetLastError());
+
+    // outputs
+    cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (genome_hits) MT_CK(cudaMemcpyAsync(genome_hits, ghits, G * 8, kind, s));
+    if (abundance) MT_CK(cudaMemcpyAsync(abundance, d_ab, G * 8, kind, s));
+    if (host_io && n_reads) {
+        MT_CK(cudaMemcpyAsync(taxon, d_taxon, n_reads * 4, cudaMemcpyDeviceToHost, s));
+        if (nloc) MT_CK(cudaMemcpyAsync(nloc, d_nloc, n_reads, cudaMemcpyDeviceToHost, s));
+        if (locs) MT_CK(cudaMemcpyAsync(locs, d_locs, n_reads * top_n * sizeof(mt_loc), cudaMemcpyDeviceToHost, s));
+    }
+    Counters h{};
+    MT_CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    dfree(ws, s);
+    MT_CK(cudaStreamSynchronize(s));
+    if (stats) {
+        stats->n_reads = n_reads;
+        stats->n_minimizers = h.stat[ST_MINS];
+        stats->n_hits = h.stat[ST_HITS];
+        stats->n_candidates = h.stat[ST_CAND];
+        stats->n_accepted = h.stat[ST_ACC];
+        stats->n_multi = h.stat[ST_MULTI];
+        stats->n_fallback = h.stat[ST_FB];
+        stats->workspace_bytes = L.total;
+    }
+    if (h.err & (ERR_BAD_BASE | ERR_BAD_OFFSETS | ERR_READ_TOO_LONG)) return MT_EINVAL;
+    if (h.err) return MT_ECUDA;
+    return MT_OK;
+}

@@ -1,0 +1,482 @@
+// Reference index on the device (Methods, "Reference Database Organisation and Index
+// Construction & Querying"): every genome's (w,k)-minimizers, found by per-thread rolling
+// windows over the 2-bit packed genomes, sorted by k-mer code (stable, so each code's
+// occurrences stay in (genome, position) order), run-length encoded and inserted into an
+// open-addressing table of 32-byte slots.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+
+namespace mt {
+
+static thread_local std::string g_last_cuda_error;
+
+void set_cuda_error(cudaError_t e, const char *what) {
+    g_last_cuda_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+bool cuda_ok(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return true;
+    set_cuda_error(e, what);
+    return false;
+}
+
+const char *last_cuda_error() { return g_last_cuda_error.c_str(); }
+
+int sm_count() {
+    static int cached = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cached < 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached = v > 0 ? v : 1;
+    }
+    return cached;
+}
+
+static std::once_flag g_pool_once;
+
+int dalloc(void **p, size_t bytes, cudaStream_t s) {
+    std::call_once(g_pool_once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;   // keep freed blocks cached in this process
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return MT_ENOMEM;
+    }
+    if (!cuda_ok(e, "cudaMallocAsync")) return MT_ECUDA;
+    return MT_OK;
+}
+
+void dfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---- 2-bit packing -----------------------------------------------------------------------
+// One thread per output word: the sequence owning the word is found by binary search over
+// the word starts (off[i]-off0 >> 5) + i, which increase strictly with i.
+__global__ void k_pack_seqs(const uint8_t *__restrict__ seq, const uint64_t *__restrict__ off,
+                            uint64_t n, uint64_t *__restrict__ words, uint64_t total_words,
+                            uint64_t off0, uint32_t *err) {
+    uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total_words) return;
+    uint64_t lo = 0, hi = n + 1;   // find the largest i in [0, n] with start(i) <= t
+    while (hi - lo > 1) {
+        uint64_t mid = (lo + hi) >> 1;
+        uint64_t sw = ((off[mid] - off0) >> 5) + mid;
+        if (sw <= t) lo = mid; else hi = mid;
+    }
+    uint64_t i = lo;
+    uint64_t sw = ((off[i] - off0) >> 5) + i;
+    if (i >= n || t < sw) { words[t] = 0; return; }
+    uint64_t j = t - sw;
+    uint64_t len = off[i + 1] - off[i];
+    if (j * 32 >= len) { words[t] = 0; return; }
+    const uint8_t *p = seq + off[i] + j * 32;
+    uint32_t m = (uint32_t)umin64(32, len - j * 32);
+    uint64_t w = 0;
+    bool bad = false;
+    for (uint32_t b = 0; b < m; b++) w |= (uint64_t)base_code(p[b], bad) << (2 * b);
+    if (bad) atomicOr(err, ERR_BAD_BASE);
+    words[t] = w;
+}
+
+int launch_pack_seqs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint64_t *words,
+                     uint64_t total_words, uint32_t *err, cudaStream_t s) {
+    if (total_words == 0) return MT_OK;
+    // off0 = 0: word starts use the absolute base offsets (header convention)
+    uint64_t blocks = (total_words + 255) / 256;
+    k_pack_seqs<<<(unsigned)blocks, 256, 0, s>>>(seq, off, n, words, total_words, 0, err);
+    MT_CK(cudaGetLastError());
+    return MT_OK;
+}
+
+// ---- genome minimizers --------------------------------------------------------------------
+struct Chunk {
+    uint32_t g;
+    uint32_t j0, j1;   // windows [j0, j1) of genome g
+};
+
+__device__ __forceinline__ void genome_kmer(const uint64_t *ref, uint64_t gw, uint64_t i,
+                                            uint32_t k, uint32_t canonical, uint64_t &code,
+                                            uint32_t &strand, uint64_t &key) {
+    uint64_t pos = i;
+    const uint64_t *base = ref + gw + (pos >> 5);
+    uint32_t sh = (uint32_t)(pos & 31u) * 2u;
+    uint64_t x = (base[0] >> sh) | ((base[1] << 1) << (63u - sh));
+    uint64_t fwd, rc;
+    kmer_codes(x, k, fwd, rc);
+    canon(fwd, rc, canonical, code, strand);
+    key = mix64(code);
+}
+
+// Sequential sliding-window minimum over windows [j0, j1) of one genome. Window j covers
+// k-mers [j, j + w). The leftmost smallest key wins; a selected position is emitted once
+// (selections never move backwards, so comparing with the previous window suffices).
+// mode 0: count only; mode 1: write (code, occ) at out + base.
+template <int MODE>
+__device__ uint32_t chunk_minimizers(const uint64_t *ref, uint64_t gw, uint32_t g, uint32_t j0,
+                                     uint32_t j1, uint32_t k, uint32_t w, uint32_t canonical,
+                                     uint64_t *out_code, uint64_t *out_occ) {
+    uint32_t start = j0 > 0 ? j0 - 1 : 0;
+    uint64_t cur_code, cur_key;
+    uint32_t cur_strand, cur_pos = start;
+    genome_kmer(ref, gw, start, k, canonical, cur_code, cur_strand, cur_key);
+    for (uint32_t t = start + 1; t < start + w; t++) {
+        uint64_t c, kk; uint32_t s;
+        genome_kmer(ref, gw, t, k, canonical, c, s, kk);
+        if (kk < cur_key) { cur_key = kk; cur_code = c; cur_strand = s; cur_pos = t; }
+    }
+    uint32_t cnt = 0;
+    uint32_t prev = 0xFFFFFFFFu;
+    uint32_t jfirst = j0;
+    if (j0 > 0) {
+        prev = cur_pos;             // selection of window j0 - 1 (owned by the previous chunk)
+        jfirst = j0;
+    } else {
+        if (MODE) { out_code[0] = cur_code; out_occ[0] = ((uint64_t)g << 33) | ((uint64_t)cur_pos << 1) | cur_strand; }
+        cnt = 1;
+        prev = cur_pos;
+        jfirst = 1;
+    }
+    for (uint32_t j = jfirst; j < j1; j++) {
+        uint32_t p = j + w - 1;
+        if (cur_pos < j) {          // the minimum left the window: rescan it
+            genome_kmer(ref, gw, j, k, canonical, cur_code, cur_strand, cur_key);
+            cur_pos = j;
+            for (uint32_t t = j + 1; t <= p; t++) {
+                uint64_t c, kk; uint32_t s;
+                genome_kmer(ref, gw, t, k, canonical, c, s, kk);
+                if (kk < cur_key) { cur_key = kk; cur_code = c; cur_strand = s; cur_pos = t; }
+            }
+        } else {
+            uint64_t c, kk; uint32_t s;
+            genome_kmer(ref, gw, p, k, canonical, c, s, kk);
+            if (kk < cur_key) { cur_key = kk; cur_code = c; cur_strand = s; cur_pos = p; }
+        }
+        if (cur_pos != prev) {
+            if (MODE) {
+                out_code[cnt] = cur_code;
+                out_occ[cnt] = ((uint64_t)g << 33) | ((uint64_t)cur_pos << 1) | cur_strand;
+            }
+            cnt++;
+            prev = cur_pos;
+        }
+    }
+    return cnt;
+}
+
+__global__ void k_genome_min_count(const uint64_t *ref, const uint64_t *gword, const Chunk *ch,
+                                   uint64_t n_chunks, uint32_t k, uint32_t w, uint32_t canonical,
+                                   uint64_t *counts) {
+    uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
+    Chunk q = ch[c];
+    counts[c] = chunk_minimizers<0>(ref, gword[q.g], q.g, q.j0, q.j1, k, w, canonical, nullptr, nullptr);
+}
+
+__global__ void k_genome_min_write(const uint64_t *ref, const uint64_t *gword, const Chunk *ch,
+                                   uint64_t n_chunks, uint32_t k, uint32_t w, uint32_t canonical,
+                                   const uint64_t *offs, uint64_t *codes, uint64_t *occs) {
+    uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chunks) return;
+    Chunk q = ch[c];
+    uint64_t o = offs[c];
+    chunk_minimizers<1>(ref, gword[q.g], q.g, q.j0, q.j1, k, w, canonical, codes + o, occs + o);
+}
+
+// ---- table insert -------------------------------------------------------------------------
+__global__ void k_insert(const uint64_t *ucode, const uint32_t *ucount, const uint64_t *uoff,
+                         const int64_t *n_keys_p, const uint64_t *occ, unsigned long long *table,
+                         uint64_t mask, uint32_t shift, uint32_t *err) {
+    uint64_t n_keys = (uint64_t)*n_keys_p;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_keys;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t code = ucode[i];
+        uint32_t cnt = ucount[i];
+        uint64_t off = uoff[i];
+        uint32_t ni = cnt <= 3 ? cnt : 0;
+        uint64_t w0 = (code + 1) | ((uint64_t)ni << 62);
+        uint64_t s = slot_of(mix64(code), shift);
+        bool done = false;
+        for (uint64_t it = 0; it <= mask; it++) {
+            unsigned long long prev = atomicCAS(&table[4 * s], 0ull, (unsigned long long)w0);
+            if (prev == 0ull) {
+                if (ni == 0) {
+                    uint64_t c24 = cnt < (1u << 24) ? cnt : (1u << 24) - 1;
+                    table[4 * s + 1] = (c24 << 40) | (off & OFF_MASK40);
+                } else {
+                    for (uint32_t t = 0; t < ni; t++) table[4 * s + 1 + t] = occ[off + t];
+                }
+                done = true;
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+        if (!done) atomicOr(err, ERR_PROBE_LIMIT);
+    }
+}
+
+}  // namespace mt
+
+using namespace mt;
+
+static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t G,
+                      const mt_index_params *p, cudaStream_t s, mt_index *ix) {
+    const uint64_t off0 = offsets[0];
+    uint64_t total = offsets[G] - off0;
+    for (uint32_t g = 0; g < G; g++) {
+        if (offsets[g + 1] < offsets[g]) return MT_EINVAL;
+        if (offsets[g + 1] - offsets[g] >= (1ull << 32)) return MT_EINVAL;
+    }
+    ix->G = G; ix->k = p->k; ix->w = p->w; ix->canonical = p->canonical ? 1 : 0;
+    ix->total_bases = total;
+    ix->h_glen.resize(G);
+    std::vector<uint64_t> hoff(G + 1), hgword(G);
+    for (uint32_t g = 0; g <= G; g++) hoff[g] = offsets[g] - off0;
+    for (uint32_t g = 0; g < G; g++) {
+        ix->h_glen[g] = hoff[g + 1] - hoff[g];
+        hgword[g] = (hoff[g] >> 5) + g;
+    }
+    ix->ref_words = (total >> 5) + G + 1;
+
+    int rc = MT_OK;
+    uint8_t *d_seq = nullptr;
+    uint64_t *d_off = nullptr;
+    uint32_t *d_err = nullptr;
+    uint32_t h_err = 0;
+    if ((rc = dalloc((void **)&d_seq, total, s))) return rc;
+    if ((rc = dalloc((void **)&d_off, (G + 1) * 8, s))) return rc;
+    if ((rc = dalloc((void **)&d_err, 4, s))) return rc;
+    MT_CK(cudaMemcpyAsync(d_seq, genomes + off0, total, cudaMemcpyHostToDevice, s));
+    MT_CK(cudaMemcpyAsync(d_off, hoff.data(), (G + 1) * 8, cudaMemcpyHostToDevice, s));
+    MT_CK(cudaMemsetAsync(d_err, 0, 4, s));
+    MT_CK(cudaMalloc((void **)&ix->d_ref, ix->ref_words * 8));
+    MT_CK(cudaMalloc((void **)&ix->d_gword, G * 8));
+    MT_CK(cudaMalloc((void **)&ix->d_glen, G * 8));
+    MT_CK(cudaMemcpyAsync(ix->d_gword, hgword.data(), G * 8, cudaMemcpyHostToDevice, s));
+    MT_CK(cudaMemcpyAsync(ix->d_glen, ix->h_glen.data(), G * 8, cudaMemcpyHostToDevice, s));
+    {
+        uint64_t blocks = (ix->ref_words + 255) / 256;
+        k_pack_seqs<<<(unsigned)blocks, 256, 0, s>>>(d_seq, d_off, G, ix->d_ref, ix->ref_words, 0, d_err);
+        MT_CK(cudaGetLastError());
+    }
+    MT_CK(cudaMemcpyAsync(&h_err, d_err, 4, cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    dfree(d_seq, s);
+    dfree(d_off, s);
+    if (h_err) { dfree(d_err, s); return MT_EINVAL; }
+
+    // chunks of windows
+    const uint32_t CH = 2048;
+    std::vector<Chunk> chunks;
+    for (uint32_t g = 0; g < G; g++) {
+        uint64_t L = ix->h_glen[g];
+        if (L < p->k) continue;
+        uint64_t nk = L - p->k + 1;
+        if (nk < p->w) continue;
+        uint64_t nwin = nk - p->w + 1;
+        for (uint64_t j = 0; j < nwin; j += CH)
+            chunks.push_back(Chunk{g, (uint32_t)j, (uint32_t)std::min<uint64_t>(nwin, j + CH)});
+    }
+    uint64_t n_chunks = chunks.size();
+    Chunk *d_ch = nullptr;
+    uint64_t *d_cnt = nullptr, *d_coff = nullptr;
+    if ((rc = dalloc((void **)&d_ch, std::max<uint64_t>(1, n_chunks) * sizeof(Chunk), s))) return rc;
+    if ((rc = dalloc((void **)&d_cnt, (n_chunks + 1) * 8, s))) return rc;
+    if ((rc = dalloc((void **)&d_coff, (n_chunks + 1) * 8, s))) return rc;
+    if (n_chunks) MT_CK(cudaMemcpyAsync(d_ch, chunks.data(), n_chunks * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+    MT_CK(cudaMemsetAsync(d_cnt, 0, (n_chunks + 1) * 8, s));
+    if (n_chunks) {
+        k_genome_min_count<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(
+            ix->d_ref, ix->d_gword, d_ch, n_chunks, p->k, p->w, ix->canonical, d_cnt);
+        MT_CK(cudaGetLastError());
+    }
+    void *d_tmp = nullptr;
+    size_t tmp_bytes = 0;
+    MT_CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_cnt, d_coff, (int64_t)(n_chunks + 1), s));
+    if ((rc = dalloc(&d_tmp, tmp_bytes, s))) return rc;
+    MT_CK(cub::DeviceScan::ExclusiveSum(d_tmp, tmp_bytes, d_cnt, d_coff, (int64_t)(n_chunks + 1), s));
+    dfree(d_tmp, s);
+    uint64_t n_occ = 0;
+    MT_CK(cudaMemcpyAsync(&n_occ, d_coff + n_chunks, 8, cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    ix->n_occ = n_occ;
+
+    uint64_t *d_code[2] = {nullptr, nullptr}, *d_val[2] = {nullptr, nullptr};
+    uint64_t nb = std::max<uint64_t>(1, n_occ) * 8;
+    if ((rc = dalloc((void **)&d_code[0], nb, s))) return rc;
+    if ((rc = dalloc((void **)&d_code[1], nb, s))) return rc;
+    if ((rc = dalloc((void **)&d_val[0], nb, s))) return rc;
+    MT_CK(cudaMalloc((void **)&d_val[1], nb));   // becomes the resident occurrence array
+    if (n_chunks) {
+        k_genome_min_write<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(
+            ix->d_ref, ix->d_gword, d_ch, n_chunks, p->k, p->w, ix->canonical, d_coff,
+            d_code[0], d_val[0]);
+        MT_CK(cudaGetLastError());
+    }
+    dfree(d_ch, s); dfree(d_cnt, s); dfree(d_coff, s);
+
+    // stable sort by code: each code's occurrences keep their (genome, position) order
+    cub::DoubleBuffer<uint64_t> kb(d_code[0], d_code[1]), vb(d_val[0], d_val[1]);
+    tmp_bytes = 0;
+    int end_bit = (int)(2 * p->k);
+    if (end_bit < 1) end_bit = 1;
+    MT_CK(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, kb, vb, (int64_t)n_occ, 0, end_bit, s));
+    if ((rc = dalloc(&d_tmp, tmp_bytes, s))) return rc;
+    MT_CK(cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, kb, vb, (int64_t)n_occ, 0, end_bit, s));
+    dfree(d_tmp, s);
+    uint64_t *codes_sorted = kb.Current();
+    uint64_t *occ_sorted = vb.Current();
+    uint64_t *code_spare = kb.Alternate();
+    uint64_t *occ_spare = vb.Alternate();
+
+    // distinct codes and their run lengths / offsets
+    uint64_t *d_ucode = code_spare;   // reuse the spare key buffer
+    uint32_t *d_ucount = nullptr;
+    uint64_t *d_uoff = nullptr;
+    int64_t *d_nruns = nullptr;
+    if ((rc = dalloc((void **)&d_ucount, std::max<uint64_t>(1, n_occ) * 4, s))) return rc;
+    if ((rc = dalloc((void **)&d_uoff, std::max<uint64_t>(1, n_occ) * 8, s))) return rc;
+    if ((rc = dalloc((void **)&d_nruns, 8, s))) return rc;
+    MT_CK(cudaMemsetAsync(d_nruns, 0, 8, s));
+    if (n_occ) {
+        tmp_bytes = 0;
+        MT_CK(cub::DeviceRunLengthEncode::Encode(nullptr, tmp_bytes, codes_sorted, d_ucode, d_ucount,
+                                                 d_nruns, (int64_t)n_occ, s));
+        if ((rc = dalloc(&d_tmp, tmp_bytes, s))) return rc;
+        MT_CK(cub::DeviceRunLengthEncode::Encode(d_tmp, tmp_bytes, codes_sorted, d_ucode, d_ucount,
+                                                 d_nruns, (int64_t)n_occ, s));
+        dfree(d_tmp, s);
+    }
+    int64_t n_keys = 0;
+    MT_CK(cudaMemcpyAsync(&n_keys, d_nruns, 8, cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    ix->n_keys = (uint64_t)n_keys;
+    if (n_keys) {
+        tmp_bytes = 0;
+        MT_CK(cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, d_ucount, d_uoff, n_keys, s));
+        if ((rc = dalloc(&d_tmp, tmp_bytes, s))) return rc;
+        MT_CK(cub::DeviceScan::ExclusiveSum(d_tmp, tmp_bytes, d_ucount, d_uoff, n_keys, s));
+        dfree(d_tmp, s);
+    }
+
+    uint64_t slots = 1024;
+    while (slots < 2 * (uint64_t)n_keys) slots <<= 1;
+    uint32_t lg = 0;
+    while ((1ull << lg) < slots) lg++;
+    ix->slots = slots;
+    ix->slot_shift = 64 - lg;
+    MT_CK(cudaMalloc((void **)&ix->d_table, slots * 32));
+    MT_CK(cudaMemsetAsync(ix->d_table, 0, slots * 32, s));
+    if (n_keys) {
+        unsigned blocks = (unsigned)std::min<uint64_t>((n_keys + 255) / 256, 65535ull * 16);
+        k_insert<<<blocks, 256, 0, s>>>(d_ucode, d_ucount, d_uoff, d_nruns, occ_sorted,
+                                         (unsigned long long *)ix->d_table, slots - 1, ix->slot_shift, d_err);
+        MT_CK(cudaGetLastError());
+    }
+    MT_CK(cudaMemcpyAsync(&h_err, d_err, 4, cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    // keep the sorted occurrence array; release the rest
+    if (occ_sorted == d_val[1]) {
+        ix->d_occ = d_val[1];
+        dfree(d_val[0], s);
+    } else {
+        // the sorted values ended in the pool buffer: move them to the resident one
+        MT_CK(cudaMemcpyAsync(d_val[1], occ_sorted, nb, cudaMemcpyDeviceToDevice, s));
+        ix->d_occ = d_val[1];
+        dfree(d_val[0], s);
+    }
+    (void)occ_spare;
+    dfree(d_code[0], s); dfree(d_code[1], s);
+    dfree(d_ucount, s); dfree(d_uoff, s); dfree(d_nruns, s); dfree(d_err, s);
+    MT_CK(cudaStreamSynchronize(s));
+    if (h_err) return MT_ECUDA;
+    ix->device_bytes = ix->ref_words * 8 + G * 16 + slots * 32 + nb;
+    return MT_OK;
+}
+
+extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
+                              const mt_index_params *p, void *stream, mt_index **out) {
+    if (!out) return MT_EINVAL;
+    *out = nullptr;
+    if (!genomes || !offsets || !p || n_genomes == 0 || n_genomes > MT_MAX_GENOMES) return MT_EINVAL;
+    if (p->k < 1 || p->k > MT_MAX_K || p->w < 1 || p->w > MT_MAX_W || p->reserved != 0) return MT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    mt_index *ix = new mt_index();
+    cudaGetDevice(&ix->device);
+    int rc = build_impl(genomes, offsets, n_genomes, p, s, ix);
+    if (rc != MT_OK) {
+        cudaStreamSynchronize(s);
+        mt_free_index(ix);
+        return rc;
+    }
+    *out = ix;
+    return MT_OK;
+}
+
+extern "C" const char *mt_last_cuda_error(void) { return mt::last_cuda_error(); }
+
+extern "C" void mt_free_index(mt_index *ix) {
+    if (!ix) return;
+    cudaFree(ix->d_ref);
+    cudaFree(ix->d_gword);
+    cudaFree(ix->d_glen);
+    cudaFree(ix->d_table);
+    cudaFree(ix->d_occ);
+    delete ix;
+}
+
+extern "C" int mt_index_get_info(const mt_index *ix, mt_index_info *info) {
+    if (!ix || !info) return MT_EINVAL;
+    info->n_genomes = ix->G;
+    info->k = ix->k;
+    info->w = ix->w;
+    info->canonical = ix->canonical;
+    info->total_bases = ix->total_bases;
+    info->n_occ = ix->n_occ;
+    info->n_keys = ix->n_keys;
+    info->table_slots = ix->slots;
+    info->device_bytes = ix->device_bytes;
+    return MT_OK;
+}
+
+extern "C" int mt_pack_seqs(const uint8_t *seq, const uint64_t *offsets, uint64_t n_seqs,
+                            uint64_t *words, void *stream) {
+    if (!seq || !offsets || !words) return MT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_seqs == 0) return MT_OK;
+    uint64_t last = 0;
+    MT_CK(cudaMemcpyAsync(&last, offsets + n_seqs, 8, cudaMemcpyDeviceToHost, s));
+    uint32_t *d_err = nullptr;
+    int rc = dalloc((void **)&d_err, 4, s);
+    if (rc) return rc;
+    MT_CK(cudaMemsetAsync(d_err, 0, 4, s));
+    MT_CK(cudaStreamSynchronize(s));
+    uint64_t total_words = (last >> 5) + n_seqs + 1;
+    rc = launch_pack_seqs(seq, offsets, n_seqs, words, total_words, d_err, s);
+    uint32_t h_err = 0;
+    if (rc == MT_OK) {
+        MT_CK(cudaMemcpyAsync(&h_err, d_err, 4, cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaStreamSynchronize(s));
+    }
+    dfree(d_err, s);
+    if (rc) return rc;
+    return h_err ? MT_EINVAL : MT_OK;
+}

@@ -1,0 +1,76 @@
+// Host-side definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mt {
+
+void set_cuda_error(cudaError_t e, const char *what);
+bool cuda_ok(cudaError_t e, const char *what);
+
+#define MT_CK(call)                                     \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (!::mt::cuda_ok(e_, #call)) return MT_ECUDA; \
+    } while (0)
+
+int sm_count();
+const char *last_cuda_error();
+
+// Stream-ordered device allocation from the default memory pool (kept cached).
+int dalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carver {
+    size_t off = 0;
+    template <typename T>
+    size_t take(uint64_t count) {
+        size_t o = (off + 255) & ~size_t(255);
+        off = o + count * sizeof(T);
+        return o;
+    }
+};
+
+}  // namespace mt
+
+struct mt_index {
+    int device = 0;
+    uint32_t G = 0, k = 0, w = 0, canonical = 0;
+    uint64_t total_bases = 0, n_occ = 0, n_keys = 0, slots = 0;
+    uint32_t slot_shift = 0;
+    uint64_t ref_words = 0;
+    uint64_t *d_ref = nullptr, *d_gword = nullptr, *d_glen = nullptr, *d_occ = nullptr;
+    ulonglong2 *d_table = nullptr;
+    uint64_t device_bytes = 0;
+    std::vector<uint64_t> h_glen;
+
+    IndexView view() const {
+        IndexView v;
+        v.table = d_table;
+        v.slot_mask = slots - 1;
+        v.slot_shift = slot_shift;
+        v.G = G;
+        v.occ = d_occ;
+        v.ref = d_ref;
+        v.gword = d_gword;
+        v.glen = d_glen;
+        v.k = k; v.w = w; v.canonical = canonical; v.pad = 0;
+        return v;
+    }
+};
+
+// Kernel launch helpers implemented in the .cu files.
+namespace mt {
+// Device scratch of one mt_classify call with host buffers and a known longest read.
+uint64_t classify_ws_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
+                           const mt_classify_params *p, uint32_t maxn, bool host_io);
+int launch_pack_seqs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint64_t *words,
+                     uint64_t total_words, uint32_t *err, cudaStream_t s);
+}

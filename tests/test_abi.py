@@ -1,0 +1,74 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every entry
+point declared in include/mt.h, and the binding's struct layouts match the header."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def mtlib():
+    from paper_2311_02029_gb300 import _build
+    _build.build()
+    import paper_2311_02029_gb300 as mt
+    return mt
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "mt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mt_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("mt_build_index", "mt_classify", "mt_eda_batch", "mt_pack_seqs", "mt_server_create",
+                 "mt_server_submit", "mt_server_poll", "mt_free_index"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(mtlib):
+    L = mtlib.lib()
+    for name in _declared():
+        assert hasattr(L, name), "libmt.so does not export %s" % name
+    assert sorted(mtlib.EXPORTS) == _declared()
+
+
+def test_struct_layouts_match_header(mtlib):
+    assert ctypes.sizeof(mtlib.IndexParams) == 16
+    assert ctypes.sizeof(mtlib.ClassifyParams) == 40
+    assert mtlib.LOC_DTYPE.itemsize == 24
+    assert ctypes.sizeof(mtlib.Stats) == 64
+    assert ctypes.sizeof(mtlib.IndexInfo) == 56
+
+
+def test_status_strings_and_argument_checks_without_gpu(mtlib):
+    L = mtlib.lib()
+    assert L.mt_version() >= 1
+    assert L.mt_strerror(0) == b"ok"
+    assert L.mt_strerror(mtlib.MT_EINVAL)
+    # argument validation happens before any CUDA call
+    out = ctypes.c_void_p()
+    p = mtlib.IndexParams(0, 10, 0, 0)          # k = 0 is out of range
+    g = np.frombuffer(b"ACGT" * 10, np.uint8)
+    off = np.array([0, 40], np.uint64)
+    rc = L.mt_build_index(ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(off.ctypes.data), 1,
+                          ctypes.byref(p), None, ctypes.byref(out))
+    assert rc == mtlib.MT_EINVAL and not out.value
+    p = mtlib.IndexParams(15, 65, 0, 0)         # w above MT_MAX_W
+    assert L.mt_build_index(ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(off.ctypes.data), 1,
+                            ctypes.byref(p), None, ctypes.byref(out)) == mtlib.MT_EINVAL
+    assert L.mt_eda_batch(None, None, 0, None, None, None, None, 5, 7, None, None) == mtlib.MT_EINVAL
+    assert L.mt_server_create(None, 1, 1, None, ctypes.byref(out)) == mtlib.MT_EINVAL
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    import paper_2311_02029_gb300 as mt
+    monkeypatch.setattr(mt, "_lib", None)
+    monkeypatch.setattr(mt, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        mt.lib()

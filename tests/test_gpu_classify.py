@@ -1,0 +1,212 @@
+"""GPU parity of the classification path (mt_build_index + mt_classify) against the oracle:
+every per-read decision, location, seed count and distance bit-exact, genome hit counts
+bit-exact, abundances within 1e-6 absolute."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import compare_classify, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2311_02029_gb300 import _build
+    _build.build()
+    import paper_2311_02029_gb300 as m
+    oracle.build()
+    return m
+
+
+def _params(c, **kw):
+    p = dict(e_abs=c["e_abs"], e_permille=c["e_permille"], min_seeds=c["min_seeds"], top_n=3, max_occ=1024,
+             cont_num=1, cont_den=10000, abund_cutoff=1e-4)
+    p.update(kw)
+    return p
+
+
+@pytest.fixture(scope="module")
+def tiny(mt):
+    c = gen.config(1)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    return c, g, r, ix, oix
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tiny_workload_host_buffers(mt, tiny, mode):
+    """8 x 50 kb genomes, k15 w10, 10,000 reads of 150 bp, E = 6, seed threshold 2."""
+    c, g, r, ix, oix = tiny
+    prm = _params(c)
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm))
+    out = mt.classify(ix, r.seq, r.offsets, eda_mode=mode, **prm)
+    compare_classify(out, ref)
+    assert out["stats"]["n_reads"] == r.n
+    assert (ref["taxon"] >= 0).mean() > 0.85
+
+
+def test_tiny_workload_device_buffers(mt, tiny):
+    import torch
+    c, g, r, ix, oix = tiny
+    prm = _params(c)
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm))
+    out = mt.classify(ix, torch.from_numpy(r.seq).cuda(), torch.from_numpy(r.offsets.astype(np.int64)).cuda(), **prm)
+    compare_classify(out, ref)
+
+
+def test_index_counts_match_oracle(mt, tiny):
+    c, g, r, ix, oix = tiny
+    info = ix.info()
+    assert info["n_occ"] == oix.n_occ
+    assert info["n_genomes"] == g.n and info["k"] == c["k"]
+
+
+@pytest.fixture(scope="module")
+def clade(mt):
+    """A scaled-down medium workload: 4 clades x 10 genomes of 100 kb at 1-10% divergence,
+    k21 w11 canonical, 20,000 reads of 150 bp on both strands, E = 8."""
+    c = gen.config(2, n_genomes=40, genome_len=100_000, n_reads=20_000)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    return c, g, r, ix, oix
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_clade_workload(mt, clade, mode):
+    c, g, r, ix, oix = clade
+    prm = _params(c)
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=8)
+    out = mt.classify(ix, r.seq, r.offsets, eda_mode=mode, **prm)
+    compare_classify(out, ref)
+    assert (ref["multi"][:, 0] >= 0).sum() > 0, "workload should contain multi-mapped reads"
+
+
+@pytest.mark.parametrize("kw", [dict(top_n=1), dict(top_n=8, min_seeds=1), dict(e_abs=0, e_permille=100),
+                                dict(max_occ=2), dict(cont_num=1, cont_den=50), dict(abund_cutoff=0.05),
+                                dict(e_abs=0, e_permille=0)])
+def test_clade_parameter_sweep(mt, clade, kw):
+    c, g, r, ix, oix = clade
+    prm = _params(c, **kw)
+    n = 4000
+    seq, off = r.seq[:int(r.offsets[n])], r.offsets[:n + 1]
+    ref = oracle.classify(oix, seq, off, oracle_params(prm), threads=8)
+    out = mt.classify(ix, seq, off, **prm)
+    compare_classify(out, ref)
+
+
+def test_mixed_lengths_and_edges(mt):
+    """Reads of 1..1024 bases (below k+w-1, exactly MT_MAX_READ_LEN), reads overhanging genome
+    ends on both strands, E from a per-mille threshold."""
+    rng = np.random.default_rng(5)
+    gs = [gen.ascii_of(rng.integers(0, 4, L, dtype=np.uint8)) for L in (3000, 1500, 5000)]
+    gseq = np.concatenate(gs)
+    goff = np.cumsum([0] + [len(x) for x in gs]).astype(np.uint64)
+    reads = []
+    for i in range(400):
+        gi = int(rng.integers(0, 3))
+        L = int(rng.choice([1, 10, 29, 30, 31, 100, 150, 251, 513, 1024]))
+        L = min(L, len(gs[gi]))
+        kind = i % 4
+        over = min(5, L // 4)
+        if kind == 0:      # starts before the genome start
+            s = np.concatenate([gen.ascii_of(rng.integers(0, 4, over, dtype=np.uint8)), gs[gi][:L - over]])
+        elif kind == 1:    # runs past the genome end
+            s = np.concatenate([gs[gi][len(gs[gi]) - (L - over):], gen.ascii_of(rng.integers(0, 4, over, dtype=np.uint8))])
+        else:
+            p = int(rng.integers(0, len(gs[gi]) - L + 1))
+            s = gs[gi][p:p + L].copy()
+        if i % 3 == 0:
+            s = gen.revcomp_ascii(s)
+        reads.append(s)
+    rseq = np.concatenate(reads)
+    roff = np.cumsum([0] + [len(x) for x in reads]).astype(np.uint64)
+    ix = mt.Index(gseq, goff, 15, 10, 1)
+    oix = oracle.Index(gseq, goff, 15, 10, 1)
+    for prm in (dict(e_abs=0, e_permille=60, min_seeds=2), dict(e_abs=5, e_permille=0, min_seeds=1, top_n=5)):
+        p = _params(dict(e_abs=0, e_permille=0, min_seeds=2), **prm)
+        ref = oracle.classify(oix, rseq, roff, oracle_params(p))
+        out = mt.classify(ix, rseq, roff, **p)
+        compare_classify(out, ref)
+
+
+def test_repeats_take_the_exact_slow_path(mt):
+    """A genome made of a repeated unit gives reads with far more seed matches than fit in
+    shared memory; they are re-mapped by the exact per-read slow path."""
+    rng = np.random.default_rng(7)
+    unit = gen.ascii_of(rng.integers(0, 4, 300, dtype=np.uint8))
+    g0 = np.concatenate([unit] * 40)
+    g1 = gen.ascii_of(rng.integers(0, 4, 20000, dtype=np.uint8))
+    gseq = np.concatenate([g0, g1])
+    goff = np.array([0, len(g0), len(g0) + len(g1)], np.uint64)
+    reads = [g0[i * 37:i * 37 + 150] for i in range(40)] + [g1[i * 400:i * 400 + 150] for i in range(40)]
+    rseq = np.concatenate(reads)
+    roff = np.cumsum([0] + [len(x) for x in reads]).astype(np.uint64)
+    ix = mt.Index(gseq, goff, 15, 10, 1)
+    oix = oracle.Index(gseq, goff, 15, 10, 1)
+    p = _params(dict(e_abs=6, e_permille=0, min_seeds=2), max_occ=64)
+    ref = oracle.classify(oix, rseq, roff, oracle_params(p))
+    out = mt.classify(ix, rseq, roff, **p)
+    compare_classify(out, ref)
+    assert out["stats"]["n_fallback"] >= 40
+
+
+def test_masked_genomes_exhaust_stored_locations(mt):
+    """Twelve genomes share one segment; only genome 0 also has a large unique part with
+    many reads. With a 1/10 cutoff genomes 1..11 are dropped, so reads of the shared segment
+    have 12 qualifying locations of which the eight stored ones hold only one kept genome:
+    the exact slow path must find the rest."""
+    rng = np.random.default_rng(11)
+    X = gen.ascii_of(rng.integers(0, 4, 2000, dtype=np.uint8))
+    Y = gen.ascii_of(rng.integers(0, 4, 60000, dtype=np.uint8))
+    gs = [np.concatenate([X, Y])] + [np.concatenate([gen.ascii_of(rng.integers(0, 4, 500, dtype=np.uint8)), X])
+                                      for _ in range(11)]
+    gseq = np.concatenate(gs)
+    goff = np.cumsum([0] + [len(x) for x in gs]).astype(np.uint64)
+    reads = [Y[i * 200:i * 200 + 150] for i in range(250)] + [X[i * 100:i * 100 + 150] for i in range(15)]
+    rseq = np.concatenate(reads)
+    roff = np.cumsum([0] + [len(x) for x in reads]).astype(np.uint64)
+    ix = mt.Index(gseq, goff, 15, 10, 0)
+    oix = oracle.Index(gseq, goff, 15, 10, 0)
+    p = _params(dict(e_abs=6, e_permille=0, min_seeds=2), cont_num=1, cont_den=10, top_n=3)
+    ref = oracle.classify(oix, rseq, roff, oracle_params(p))
+    assert ref["keep"].tolist() == [1] + [0] * 11
+    out = mt.classify(ix, rseq, roff, **p)
+    compare_classify(out, ref)
+    assert out["stats"]["n_fallback"] >= 15
+
+
+def test_invalid_inputs(mt, tiny):
+    c, g, r, ix, oix = tiny
+    prm = _params(c)
+    bad = r.seq[:300].copy()
+    bad[170] = ord("N")
+    with pytest.raises(mt.MtError) as e:
+        mt.classify(ix, bad, np.array([0, 150, 300], np.uint64), **prm)
+    assert e.value.status == mt.MT_EINVAL
+    long = np.frombuffer(b"ACGT" * 300, np.uint8)
+    with pytest.raises(mt.MtError):
+        mt.classify(ix, long, np.array([0, 1200], np.uint64), **prm)
+    with pytest.raises(mt.MtError):
+        mt.classify(ix, r.seq[:300], np.array([0, 200, 100], np.uint64), **prm)
+    with pytest.raises(mt.MtError):
+        mt.classify(ix, r.seq[:300], np.array([0, 150], np.uint64), **dict(prm, top_n=9))
+    # the library is still usable afterwards
+    out = mt.classify(ix, r.seq[:1500], r.offsets[:11], **prm)
+    ref = oracle.classify(oix, r.seq[:1500], r.offsets[:11], oracle_params(prm))
+    compare_classify(out, ref)
+
+
+def test_empty_batch(mt, tiny):
+    c, g, r, ix, oix = tiny
+    out = mt.classify(ix, np.zeros(0, np.uint8), np.zeros(1, np.uint64), **_params(c))
+    assert len(out["taxon"]) == 0
+    assert out["genome_hits"].tolist() == [0] * g.n
+    assert out["abundance"].tolist() == [0.0] * g.n

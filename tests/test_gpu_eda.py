@@ -1,0 +1,131 @@
+"""GPU parity of the edit-distance-approximation stage alone (mt_pack_seqs + mt_eda_batch)
+against the oracle, in both execution forms."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2311_02029_gb300 import _build
+    _build.build()
+    import paper_2311_02029_gb300 as m
+    oracle.build()
+    return m
+
+
+def np_pack(seq: np.ndarray, off: np.ndarray) -> np.ndarray:
+    """Reference of the documented packed layout: base j of sequence i at bits 2*(j%32) of
+    word (off[i] >> 5) + i + j // 32, codes A0 C1 G2 T3."""
+    code = np.zeros(256, np.uint64)
+    for i, b in enumerate(b"ACGT"):
+        code[b] = i
+    n = len(off) - 1
+    words = np.zeros(int(off[-1]) // 32 + n + 1, np.uint64)
+    for i in range(n):
+        s = seq[int(off[i]):int(off[i + 1])]
+        base = int(off[i]) // 32 + i
+        for j in range(0, len(s), 32):
+            c = code[s[j:j + 32]]
+            words[base + j // 32] = np.bitwise_or.reduce(c << (2 * np.arange(len(c), dtype=np.uint64)))
+    return words
+
+
+def to_dev(pairs, mt):
+    import torch
+    dev = "cuda"
+    rs = torch.from_numpy(pairs.read_seq).to(dev)
+    ro = torch.from_numpy(pairs.read_off.astype(np.int64)).to(dev)
+    ws = torch.from_numpy(pairs.win_seq).to(dev)
+    wo = torch.from_numpy(pairs.win_off.astype(np.int64)).to(dev)
+    rw = mt.pack_seqs(rs, ro, mt.packed_words(pairs.read_off))
+    ww = mt.pack_seqs(ws, wo, mt.packed_words(pairs.win_off))
+    pr = torch.from_numpy(pairs.pair_read.astype(np.int32)).to(dev)
+    E = torch.from_numpy(pairs.E.astype(np.int16)).to(dev)
+    return rw, ro, ww, wo, pr, E
+
+
+def test_pack_matches_layout(mt):
+    import torch
+    rng = np.random.default_rng(1)
+    lens = rng.integers(0, 100, 300)
+    off = np.zeros(301, np.uint64)
+    off[1:] = np.cumsum(lens) + 7          # non-zero first offset
+    off[0] = 7
+    seq = gen.ascii_of(rng.integers(0, 4, int(off[-1]), dtype=np.uint8))
+    words = mt.pack_seqs(torch.from_numpy(seq).cuda(), torch.from_numpy(off.astype(np.int64)).cuda(),
+                         mt.packed_words(off))
+    exp = np_pack(seq, off)
+    got = words.cpu().numpy().view(np.uint64)
+    # words before the first sequence are not part of the layout
+    first = int(off[0]) // 32
+    assert np.array_equal(got[first:], exp[first:])
+
+
+def test_pack_rejects_bad_bases(mt):
+    import torch
+    seq = np.frombuffer(b"ACGTNACGT", np.uint8).copy()
+    off = np.array([0, 9], np.int64)
+    with pytest.raises(mt.MtError):
+        mt.pack_seqs(torch.from_numpy(seq).cuda(), torch.from_numpy(off).cuda(), 2)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_eda_batch_matches_oracle(mt, mode):
+    """Reads of 100-250 bp, E in {2,4,6,10}% of n, 70% of windows within E planted edits."""
+    pairs = gen.make_eda_pairs(gen.config(3), n_pairs=200_000, seed=77)
+    dist = mt.eda_batch(*to_dev(pairs, mt), mode=mode).cpu().numpy()
+    ref = oracle.eda_batch(pairs, threads=8)
+    bad = np.flatnonzero(dist != ref)
+    assert len(bad) == 0, "%d pairs differ, first %s gpu %s oracle %s" % (len(bad), bad[:5], dist[bad[:5]], ref[bad[:5]])
+    assert 0.3 < (ref <= pairs.E).mean() < 0.95
+
+
+def test_eda_batch_extreme_shapes(mt):
+    """E = 0 and E = 127, reads of 1 and 1024 bases, in one call (several classes)."""
+    rng = np.random.default_rng(3)
+    reads, wins, pr, Es = [], [], [], []
+    for i in range(600):
+        n = int(rng.choice([1, 2, 31, 32, 33, 64, 500, 1024]))
+        E = int(rng.choice([0, 1, 5, 31, 64, 127]))
+        r = gen.ascii_of(rng.integers(0, 4, n, dtype=np.uint8))
+        w = gen.ascii_of(rng.integers(0, 4, n + 2 * E, dtype=np.uint8))
+        if i % 2:
+            s = int(rng.integers(0, 2 * E + 1))
+            w[s:s + n] = r
+            if n > 4:
+                w[s + n // 2] = ord("A") if r[n // 2] != ord("A") else ord("C")
+        reads.append(r)
+        wins.append(w)
+        pr.append(i)
+        Es.append(E)
+    pairs = gen.EdaPairs(read_seq=np.concatenate(reads), read_off=np.cumsum([0] + [len(x) for x in reads]).astype(np.uint64),
+                         win_seq=np.concatenate(wins), win_off=np.cumsum([0] + [len(x) for x in wins]).astype(np.uint64),
+                         pair_read=np.array(pr, np.uint32), E=np.array(Es, np.uint16), planted=np.zeros(len(pr), np.uint16))
+    ref = oracle.eda_batch(pairs)
+    for mode in (0, 1):
+        dist = mt.eda_batch(*to_dev(pairs, mt), mode=mode).cpu().numpy()
+        assert np.array_equal(dist, ref), mode
+
+
+def test_eda_batch_rejects_bad_pairs(mt):
+    import torch
+    pairs = gen.make_eda_pairs(gen.config(3), n_pairs=1000, seed=5)
+    rw, ro, ww, wo, pr, E = to_dev(pairs, mt)
+    E2 = E.clone()
+    E2[10] += 1                      # window length no longer n + 2E
+    with pytest.raises(mt.MtError):
+        mt.eda_batch(rw, ro, ww, wo, pr, E2)
+    E3 = E.clone()
+    E3[3] = 200                      # above MT_MAX_E
+    with pytest.raises(mt.MtError):
+        mt.eda_batch(rw, ro, ww, wo, pr, E3)
+    d = mt.eda_batch(rw, ro, ww, wo, pr, E)   # still usable
+    assert d.numel() == 1000
+    torch.cuda.synchronize()
