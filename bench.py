@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MetaTrinity hot path; prints ONE JSON line on rank 0.
+
+A step is one mt_classify call over one batch of the medium workload (200 genomes x 2 Mb in
+20 clades x 10 at 1-10% divergence, k21 w11 canonical, 10^7 reads of 150 bp, E = 8): packing,
+minimizers, index lookups, containment counts, locations, SneakySnake on every candidate and
+the abundance profile. Inputs are resident in HBM when the timed region starts (1.5 GB of
+reads, larger than L2). `value` is reads/s of the batched form; the plain form, the
+end-to-end form with host buffers, the edit-distance stage alone on the batching workload
+(read-versus-window pairs) and a serving sample are reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact); p50/p99"
+WORKLOAD = ("medium: 200 genomes x 2 Mb (20 clades x 10, 1-10% divergence), k21 w11 canonical, "
+            "1e7 reads x 150 bp (both strands, 0.5% subst + 0.05% indel, 5% random), E=8, min_seeds 3, top 3")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region (SM clock, max clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu)
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def params(c, mode):
+    return dict(e_abs=c["e_abs"], e_permille=c["e_permille"], min_seeds=c["min_seeds"], top_n=3, max_occ=1024,
+                cont_num=1, cont_den=10000, abund_cutoff=1e-4, eda_mode=mode)
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the oracle, timed on host cores
+# ---------------------------------------------------------------------------------------------
+def run_reference(args):
+    import oracle
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    c = gen.config(2)
+    t0 = time.time()
+    g = gen.make_genomes(c)
+    reads = gen.make_reads(c, g)
+    log("[ref] data %.1fs" % (time.time() - t0))
+    t0 = time.time()
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    log("[ref] oracle index %.1fs" % (time.time() - t0))
+    p = oracle.params(**{k: v for k, v in params(c, 0).items() if k != "eda_mode"})
+    S = args.ref_sample
+    rng = np.random.default_rng(1234)
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = np.sort(rng.choice(reads.n, S, replace=False))
+        sub = gen.subsample_reads(reads, idx)
+        t = time.perf_counter()
+        oracle.classify(oix, sub.seq, sub.offsets, p, threads=1)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1000.0 * statistics.mean(times)
+    v = S / (ms / 1000.0)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "reads/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reads": c["n_reads"], "genomes": c["n_genomes"]},
+            "cpu_baseline": {"value": v, "unit": "reads/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d random reads of the workload per step (containment over the sample)" % S},
+            "e2e": {"value": v, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def timed_steps(fn, steps, warmup, stream, torch):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    outs = []
+    e0.record(stream)
+    for _ in range(steps):
+        outs.append(fn())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, outs
+
+
+def eda_stage(mt, torch, n_pairs, steps, warmup):
+    c3 = gen.config(3)
+    t0 = time.time()
+    pairs = gen.make_eda_pairs(c3, n_pairs=n_pairs)
+    log("[eda] %d pairs generated in %.1fs" % (pairs.n_pairs, time.time() - t0))
+    dev = "cuda"
+    rs = torch.from_numpy(pairs.read_seq).to(dev)
+    ro = torch.from_numpy(pairs.read_off.astype(np.int64)).to(dev)
+    rw = mt.pack_seqs(rs, ro, mt.packed_words(pairs.read_off))
+    del rs
+    ws = torch.from_numpy(pairs.win_seq).to(dev)
+    wo = torch.from_numpy(pairs.win_off.astype(np.int64)).to(dev)
+    ww = mt.pack_seqs(ws, wo, mt.packed_words(pairs.win_off))
+    del ws
+    pr = torch.from_numpy(pairs.pair_read.astype(np.int32)).to(dev)
+    E = torch.from_numpy(pairs.E.astype(np.int16)).to(dev)
+    stream = torch.cuda.current_stream()
+    res = {}
+    outs = {}
+    for name, mode in (("batched", mt.MT_EDA_BATCHED), ("plain", mt.MT_EDA_PLAIN)):
+        ms, o = timed_steps(lambda: mt.eda_batch(rw, ro, ww, wo, pr, E, mode=mode), steps, warmup, stream, torch)
+        res[name] = pairs.n_pairs / (ms / 1000.0)
+        res["ms_" + name] = ms
+        outs[name] = o[-1]
+    same = bool(torch.equal(outs["batched"], outs["plain"]))
+    accepted = float((outs["batched"].cpu().numpy() <= pairs.E).mean())
+    window_bytes = int(pairs.win_off[-1])
+    return {"workload": "batching: %d read-vs-window pairs, n~U[100,250], E in {2,4,6,10}%% of n, "
+                        "geometric(6) candidates per read, %d reads" % (pairs.n_pairs, pairs.n_reads),
+            "pairs_per_s_batched": res["batched"], "pairs_per_s_plain": res["plain"],
+            "ms_batched": res["ms_batched"], "ms_plain": res["ms_plain"],
+            "batched_over_plain": res["batched"] / res["plain"], "identical": same,
+            "accepted_frac": accepted, "window_bases": window_bytes}
+
+
+def serving_sample(mt, ix, reads, c, seconds, torch):
+    """Poisson arrivals at 20 batches/s, log-uniform 1k-1M reads per batch drawn from the
+    medium workload's reads; p50/p99 of submit-to-result latency."""
+    c4 = gen.config(4)
+    n_batches = max(1, int(seconds * c4["rate"]))
+    t_arr, sizes = gen.make_arrivals(c4, n_batches=n_batches)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.5)
+    srv = mt.Server(ix, budget, max_slots=4, **params(c, mt.MT_EDA_BATCHED))
+    rng = np.random.default_rng(99)
+    ids = []
+    lat = []
+    done_reads = 0
+    pending = {}
+    lock = threading.Lock()
+    stop = [False]
+
+    def poller():
+        nonlocal done_reads
+        while True:
+            with lock:
+                items = list(pending.items())
+            if not items and stop[0]:
+                return
+            for rid, n in items:
+                rc, l, out = srv.poll(rid, 0)
+                if rc in (mt.MT_EBUSY, mt.MT_ETIMEDOUT):
+                    continue
+                with lock:
+                    del pending[rid]
+                if rc == mt.MT_OK:
+                    lat.append(l)
+                    done_reads += n
+            time.sleep(0.0005)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for ta, sz in zip(t_arr, sizes):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        sz = int(min(sz, reads.n))
+        a = int(rng.integers(0, reads.n - sz + 1))
+        b0, b1 = int(reads.offsets[a]), int(reads.offsets[a + sz])
+        off = (reads.offsets[a:a + sz + 1] - np.uint64(b0)).astype(np.uint64)
+        rid = srv.submit(reads.seq[b0:b1], off)
+        with lock:
+            pending[rid] = sz
+        ids.append(rid)
+    stop[0] = True
+    th.join()
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat_ms = np.array(lat) * 1000.0
+    return {"workload": "serving: medium-workload index resident; Poisson 20 batches/s, "
+                        "log-uniform 1k-1M reads per batch; %d batches (%.0f s of arrivals)" % (n_batches, t_arr[-1]),
+            "reads_per_s": done_reads / wall, "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+            "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None, "completed": len(lat_ms),
+            "offered_reads_per_s": float(sizes.sum() / max(t_arr[-1], 1e-9)), "hbm_budget_bytes": budget,
+            "slots": 4}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2311_02029_gb300 as mt
+    from paper_2311_02029_gb300 import _build
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    mt.lib()
+
+    c = gen.config(2, n_reads=args.reads)
+    t0 = time.time()
+    g = gen.make_genomes(c)
+    reads = gen.make_reads(c, g, seed=c["seed"] + rank)
+    log("[ours] data %.1fs" % (time.time() - t0))
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    index_s = time.time() - t0
+    info = ix.info()
+    log("[ours] index %.1fs %s" % (index_s, info))
+
+    d_reads = torch.from_numpy(reads.seq).cuda()
+    d_off = torch.from_numpy(reads.offsets.astype(np.int64)).cuda()
+    n_reads, n_bases = reads.n, int(reads.offsets[-1])
+
+    def step(mode):
+        return lambda: mt.classify(ix, d_reads, d_off, **params(c, mode))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # batched form (the headline); clocks sampled during its timed region
+    for _ in range(args.warmup):
+        step(mt.MT_EDA_BATCHED)()
+    barrier()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = step(mt.MT_EDA_BATCHED)()
+        stats.append(out["stats"])
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_reads / (ms / 1000.0)
+    batched_out = out
+
+    # plain form on the same inputs: identical outputs required
+    ms_plain, outs = timed_steps(step(mt.MT_EDA_PLAIN), args.steps, 1, stream, torch)
+    plain_out = outs[-1]
+    identical = (torch.equal(batched_out["taxon"], plain_out["taxon"])
+                 and torch.equal(batched_out["locs"], plain_out["locs"])
+                 and torch.equal(batched_out["genome_hits"], plain_out["genome_hits"])
+                 and bool((batched_out["abundance"] - plain_out["abundance"]).abs().max().item() <= 1e-6))
+
+    # end to end: pinned host buffers, copies inside the timed region
+    h_reads = torch.from_numpy(reads.seq).pin_memory()
+    h_off = torch.from_numpy(reads.offsets.astype(np.int64)).pin_memory()
+    top_n = 3
+    G = g.n
+    def pinned(shape, dtype):
+        return torch.empty(int(np.prod(shape)) * np.dtype(dtype).itemsize, dtype=torch.uint8).pin_memory() \
+            .numpy().view(dtype).reshape(shape)
+    h_out = dict(taxon=pinned((n_reads,), np.int32), nloc=pinned((n_reads,), np.uint8),
+                 locs=pinned((n_reads, top_n), mt.LOC_DTYPE), genome_hits=pinned((G,), np.uint64),
+                 abundance=pinned((G,), np.float64))
+    e2e_ms, _ = timed_steps(lambda: mt.classify(ix, h_reads.numpy(), h_off.numpy().view(np.uint64),
+                                                out=h_out, **params(c, mt.MT_EDA_BATCHED)),
+                            max(1, args.steps // 2), 1, stream, torch)
+    h2d = n_bases + (n_reads + 1) * 8
+    d2h = n_reads * (4 + 1 + 24 * top_n) + G * 16
+
+    # roofline of the dominant kernel (the seeding pass): algorithmic bytes per launch
+    st = {k: statistics.mean(s[k] for s in stats) for k in stats[0]}
+    seed_bytes = (n_bases                          # read bytes in
+                  + (n_bases / 32.0 + n_reads) * 8  # packed reads out
+                  + st["n_minimizers"] * 32         # one 32-byte slot per lookup
+                  + st["n_ext_occ"] * 8             # occurrences outside the slot
+                  + n_reads * 4 + st["n_stored"] * 16)   # location counts and records out
+    hbm, peak_kind = peaks()
+    achieved = seed_bytes / (st["ms_seed"] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": args.seed_traffic, "kernel": "k_seed",
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
+                "algorithmic_bytes_per_launch": seed_bytes, "ms_per_launch": st["ms_seed"],
+                "stage_ms": {k[3:]: st[k] for k in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")}}
+
+    line = {"metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded generator; the paper's CAMI reads "
+                                                            "and NCBI database are not available)",
+            "config": {"workload": WORKLOAD, "reads": n_reads, "genomes": g.n, "reference_bases": int(g.offsets[-1]),
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (%.2f GB reads, %.2f GB index)" % (n_bases / 1e9, info["device_bytes"] / 1e9)},
+            "pairs_per_s": st["n_candidates"] / (ms / 1000.0) * world,
+            "plain": {"value": world * n_reads / (ms_plain / 1000.0), "ms_per_step": ms_plain, "identical": identical},
+            "roofline": roofline,
+            "e2e": {"value": world * n_reads / (e2e_ms / 1000.0), "unit": "reads/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "clocks": clocks, "gpu_launches": int(st["n_launches"]) * args.steps,
+            "index": {"build_s": index_s, **info},
+            "counts_per_step": {k: st[k] for k in ("n_minimizers", "n_hits", "n_candidates", "n_accepted",
+                                                   "n_multi", "n_fallback", "n_ext_occ", "n_stored")}}
+
+    if rank == 0 and world == 1 and args.eda_pairs > 0:
+        t0 = time.time()
+        line["eda_stage"] = eda_stage(mt, torch, args.eda_pairs, max(1, args.steps // 2), 1)
+        log("[ours] eda stage %.1fs" % (time.time() - t0))
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.serve_seconds > 0:
+        t0 = time.time()
+        line["serving"] = serving_sample(mt, ix, reads, c, args.serve_seconds, torch)
+        log("[ours] serving %.1fs" % (time.time() - t0))
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        import oracle
+        t0 = time.time()
+        oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+        rng = np.random.default_rng(4321)
+        idx = np.sort(rng.choice(reads.n, args.cpu_sample, replace=False))
+        sub = gen.subsample_reads(reads, idx)
+        p = oracle.params(**{k: v for k, v in params(c, 0).items() if k != "eda_mode"})
+        t = time.perf_counter()
+        oracle.classify(oix, sub.seq, sub.offsets, p, threads=1)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": args.cpu_sample / dt, "unit": "reads/s", "cores": 1, "kind": "oracle",
+                                "sample": "%d random reads of the workload, one thread, index prebuilt "
+                                          "(host has %d cores)" % (args.cpu_sample, len(os.sched_getaffinity(0))),
+                                "seconds": dt}
+        log("[ours] cpu baseline %.1fs" % (time.time() - t0))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--reads", type=int, default=gen.CONFIGS[2]["n_reads"])
+    ap.add_argument("--eda-pairs", type=int, default=gen.CONFIGS[3]["n_pairs"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--ref-sample", type=int, default=20_000)
+    ap.add_argument("--seed-traffic", type=float, default=None,
+                    help="ncu dram bytes per seeding launch, scaled to the full batch")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -85,7 +85,8 @@ typedef struct {
     uint8_t pad[6];
 } mt_loc;
 
-/* Optional per-call counters. */
+/* Optional per-call counters and stage times. The stage times are CUDA-event intervals
+ * recorded on the call's stream around each stage's kernels. */
 typedef struct {
     uint64_t n_reads;
     uint64_t n_minimizers;   /* read minimizers looked up */
@@ -95,6 +96,14 @@ typedef struct {
     uint64_t n_multi;        /* accepted reads whose best distance is shared by >1 genome */
     uint64_t n_fallback;     /* reads re-mapped by the exact slow path (hit overflow) */
     uint64_t workspace_bytes;
+    uint64_t n_ext_occ;      /* occurrences read from the occurrence array (not inline) */
+    uint64_t n_stored;       /* location records written by the seeding pass */
+    uint64_t n_launches;     /* kernels launched by the call */
+    double ms_seed;          /* seeding, lookup, containment counts, locations */
+    double ms_select;        /* containment mask, candidate selection, slow path */
+    double ms_eda;           /* edit-distance approximation */
+    double ms_profile;       /* per-read decision, multi-read split, abundances */
+    double ms_total;         /* first to last kernel of the call */
 } mt_stats;
 
 typedef struct {

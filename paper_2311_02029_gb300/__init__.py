@@ -53,10 +53,12 @@ class ClassifyParams(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("n_reads", "n_minimizers", "n_hits", "n_candidates", "n_accepted", "n_multi",
-                 "n_fallback", "workspace_bytes")]
+                 "n_fallback", "workspace_bytes", "n_ext_occ", "n_stored", "n_launches")] + \
+               [(n, ctypes.c_double) for n in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")]
 
     def as_dict(self):
-        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+        return {n: (float(getattr(self, n)) if n.startswith("ms_") else int(getattr(self, n)))
+                for n, _ in self._fields_}
 
 
 class IndexInfo(ctypes.Structure):
@@ -205,9 +207,10 @@ def classify_params(e_abs=0, e_permille=100, min_seeds=3, top_n=3, max_occ=1024,
                           abund_cutoff)
 
 
-def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, **params) -> dict:
+def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None, **params) -> dict:
     """``mt_classify`` over one read batch. ``reads``/``offsets`` are either host arrays
-    (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors)."""
+    (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors).
+    ``out`` may hold preallocated host output arrays (e.g. in pinned memory)."""
     p = classify_params(**params)
     st = Stats()
     G = ix.n_genomes
@@ -227,9 +230,12 @@ def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, **params
         r = _host_u8(reads)
         off = _host_u64(offsets)
         n_reads = len(off) - 1
-        out = dict(taxon=np.empty(n_reads, np.int32), nloc=np.empty(n_reads, np.uint8),
-                   locs=np.empty((n_reads, p.top_n), LOC_DTYPE) if want_locs else None,
-                   genome_hits=np.empty(G, np.uint64), abundance=np.empty(G, np.float64))
+        if out is None:
+            out = dict(taxon=np.empty(n_reads, np.int32), nloc=np.empty(n_reads, np.uint8),
+                       locs=np.empty((n_reads, p.top_n), LOC_DTYPE) if want_locs else None,
+                       genome_hits=np.empty(G, np.uint64), abundance=np.empty(G, np.float64))
+        else:
+            out = dict(out)
         rc = lib().mt_classify(ix.handle, _ptr(r), len(r), _ptr(off), n_reads, ctypes.byref(p), 0,
                                _stream(stream), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
                                _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))

@@ -56,7 +56,7 @@ struct WarpSmem {
     uint16_t qs[HCAP];
 };
 
-enum StatIdx { ST_MINS = 0, ST_HITS, ST_CAND, ST_ACC, ST_MULTI, ST_FB, ST_N };
+enum StatIdx { ST_MINS = 0, ST_HITS, ST_CAND, ST_ACC, ST_MULTI, ST_FB, ST_EXT, ST_STORED, ST_N };
 
 struct Counters {
     uint32_t err;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
     }
     unsigned long long *H_out = SMEM_HIST ? hist : A.ghits;
     const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
-    unsigned long long n_mins = 0, n_hits = 0;
+    unsigned long long n_mins = 0, n_hits = 0, n_ext = 0, n_stored = 0;
 
     const uint64_t total_warps = (uint64_t)gridDim.x * SEED_WARPS;
     for (uint64_t r = (uint64_t)blockIdx.x * SEED_WARPS + warp; r < A.n_reads; r += total_warps) {
@@ -253,6 +253,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
                     rpos = ws.mpos[m];
                     L = probe(A.ix, cs & CODE_MASK62, ws.mkey[m], &A.ctr->err);
                     cnt = L.cnt <= A.max_occ ? L.cnt : 0;
+                    if (!L.ninline) n_ext += cnt;
                 }
                 uint32_t incl = warp_incl_scan(cnt);
                 uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -331,12 +332,15 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
                 A.clus[r * CSTORE + rank] = c;
             }
         }
-        if (lane == 0) A.qcnt[r] = Q;
+        if (lane == 0) { A.qcnt[r] = Q; n_stored += min(Q, CSTORE); }
         __syncwarp();
     }
+    for (int o = 16; o > 0; o >>= 1) n_ext += __shfl_xor_sync(FULL, n_ext, o);
     if (lane == 0) {
         atomicAdd(&A.ctr->stat[ST_MINS], n_mins);
         atomicAdd(&A.ctr->stat[ST_HITS], n_hits);
+        atomicAdd(&A.ctr->stat[ST_EXT], n_ext);
+        atomicAdd(&A.ctr->stat[ST_STORED], n_stored);
     }
     if (SMEM_HIST) {
         __syncthreads();
@@ -856,6 +860,14 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
     MT_CK(cudaMemsetAsync(M, 0, G * 8, s));
 
     IndexView iv = ix->view();
+    // stage timing on the call's stream (only when counters are requested)
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    const bool timing = stats != nullptr;
+    if (timing)
+        for (auto &e : ev) MT_CK(cudaEventCreate(&e));
+    auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
+    uint64_t launches = host_io ? 0 : (n_reads ? 1 : 0);   // k_maxlen
+    mark(0);
     if (n_reads) {
         SeedArgs A;
         A.ix = iv;
@@ -888,6 +900,7 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
         if (smem_hist) k_seed<true><<<grid, SEED_THREADS, smem, s>>>(A);
         else k_seed<false><<<grid, SEED_THREADS, smem, s>>>(A);
         MT_CK(cudaGetLastError());
+        mark(1);
 
         k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
         MT_CK(cudaGetLastError());
@@ -913,12 +926,15 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
         F.cap = L.fb_cap;
         k_fallback<<<FB_CTAS, FB_THREADS, 0, s>>>(F);
         MT_CK(cudaGetLastError());
+        mark(2);
 
         rc = launch_classify_eda(iv, A.rw, d_roff, off0, (const uint32_t *)P(L.cl), &ctr->cl_count,
                                  n_reads * top_n, (const Cluster *)P(L.cand), top_n, p->e_abs, p->e_permille,
                                  std::max<uint32_t>(maxn, 1), maxE, p->eda_mode, (uint8_t *)P(L.dist),
                                  &ctr->eda_counter, s);
         if (rc) { dfree(ws, s); return rc; }
+        mark(3);
+        launches += 5;   // seed, mask, select, fallback, approximation
 
         DecideArgs D;
         D.n_reads = n_reads; D.roff = d_roff;
@@ -935,10 +951,15 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
         MT_CK(cudaGetLastError());
         k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(D.multi_list, ctr, D.multi_set, top_n, U, M);
         MT_CK(cudaGetLastError());
+        launches += 2;
+    } else {
+        mark(1); mark(2); mark(3);
     }
     double *d_ab = (double *)P(L.abund);
     k_abund<<<1, 1024, 0, s>>>(G, U, M, p->abund_cutoff, d_ab);
     MT_CK(cudaGetLastError());
+    launches += 1;
+    mark(4);
 
     // outputs
     cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -962,6 +983,18 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
         stats->n_multi = h.stat[ST_MULTI];
         stats->n_fallback = h.stat[ST_FB];
         stats->workspace_bytes = L.total;
+        stats->n_ext_occ = h.stat[ST_EXT];
+        stats->n_stored = h.stat[ST_STORED];
+        stats->n_launches = launches;
+        float t[4] = {0, 0, 0, 0}, tot = 0;
+        for (int i = 0; i < 4; i++) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+        cudaEventElapsedTime(&tot, ev[0], ev[4]);
+        stats->ms_seed = t[0];
+        stats->ms_select = t[1];
+        stats->ms_eda = t[2];
+        stats->ms_profile = t[3];
+        stats->ms_total = tot;
+        for (auto &e : ev) cudaEventDestroy(e);
     }
     if (h.err & (ERR_BAD_BASE | ERR_BAD_OFFSETS | ERR_READ_TOO_LONG)) return MT_EINVAL;
     if (h.err) return MT_ECUDA;
