@@ -34,8 +34,8 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const uint64_t 
 static constexpr unsigned FULL = 0xffffffffu;
 static constexpr int SEED_WARPS = 8;
 static constexpr int SEED_THREADS = SEED_WARPS * 32;
-static constexpr uint32_t TILE = 64;                      // windows per tile
-static constexpr uint32_t KEYS = TILE + MT_MAX_W;         // k-mers a tile may need (<= TILE+w-1)
+static constexpr uint32_t TILE = 128;                     // windows per tile
+static constexpr uint32_t KEYS = TILE + MT_MAX_W + 4;     // k-mers a tile may read (<= TILE+w+2)
 static constexpr uint32_t HCAP = 256;                     // seed matches held per read
 static constexpr uint32_t RDW = MT_MAX_READ_LEN / 32 + 2;
 static constexpr uint32_t CSTORE = 8;                     // locations stored per read
@@ -45,17 +45,19 @@ static constexpr int FB_CTAS = 16;
 static constexpr int FB_THREADS = 256;
 
 struct WarpSmem {
-    uint64_t rd[RDW];
-    uint64_t key[KEYS];
-    uint64_t code[KEYS];      // code | strand << 63
-    uint64_t mcode[TILE];
-    uint64_t mkey[TILE];
-    uint64_t hits[HCAP];
-    uint16_t mpos[TILE];
-    uint16_t nxt[HCAP];
-    uint16_t qs[HCAP];
+    uint64_t rd[RDW];           // packed read
+    uint64_t key[KEYS];         // k-mer keys of the tile
+    uint64_t hits[HCAP];        // seed-match keys
+    uint64_t inl[32 * 3];       // inline occurrences of the 32 lookups in flight
+    uint64_t off[32];           // occurrence-list offsets of the lookups in flight
+    uint32_t pref[33];          // exclusive prefix of match counts of the lookups in flight
+    uint32_t meta[32];          // rpos | strand << 16 | ninline << 17
+    uint16_t mpos[TILE];        // minimizer positions of the tile
+    uint16_t gs[HCAP + 1];      // starts of (genome, strand) groups in the sorted matches
+    uint16_t qs[HCAP];          // qualifying locations: first match
+    uint16_t qn[HCAP];          //                       seed count
+    uint32_t qcount;
 };
-
 enum StatIdx { ST_MINS = 0, ST_HITS, ST_CAND, ST_ACC, ST_MULTI, ST_FB, ST_EXT, ST_STORED, ST_N };
 
 struct Counters {
@@ -88,6 +90,27 @@ struct SeedArgs {
 };
 
 // ---- read packing (one warp) ------------------------------------------------------------
+// Four bytes at a time: code = ((b >> 1) & 3) with G/T swapped; a byte is valid iff the
+// ASCII letter of its code (picked with a byte permute from "ACGT") equals the byte.
+MT_DEV uint32_t swar_pack4(uint32_t u, uint32_t inmask, bool &bad) {
+    uint32_t c = (u >> 1) & 0x03030303u;
+    c ^= (c >> 1) & 0x01010101u;
+    c &= inmask;
+    uint32_t sel = (c & 0x3u) | ((c >> 4) & 0x30u) | ((c >> 8) & 0x300u) | ((c >> 12) & 0x3000u);
+    uint32_t exp = __byte_perm(0x54474341u, 0u, sel);
+    bad |= ((exp ^ u) & inmask) != 0u;
+    return (c & 0x3u) | ((c >> 6) & 0xCu) | ((c >> 12) & 0x30u) | ((c >> 18) & 0xC0u);
+}
+
+MT_DEV uint32_t byte_mask(int64_t lo, int64_t hi) {   // bytes [lo, hi) of a 4-byte word
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > 4 ? 4 : hi;
+    if (hi <= lo) return 0u;
+    uint32_t m_hi = hi >= 4 ? 0xFFFFFFFFu : ((1u << (8 * hi)) - 1u);
+    uint32_t m_lo = (1u << (8 * lo)) - 1u;
+    return m_hi & ~m_lo;
+}
+
 MT_DEV bool warp_pack(const uint8_t *reads, uint64_t n_bases, int vec_ok, uint64_t start, uint32_t n,
                       uint64_t *rd) {
     const uint32_t lane = lane_id();
@@ -98,25 +121,30 @@ MT_DEV bool warp_pack(const uint8_t *reads, uint64_t n_bases, int vec_ok, uint64
     const uint32_t nch = (uint32_t)((end - A + 15) >> 4);
     bool bad = false;
     for (uint32_t c = lane; c < nch; c += 32) {
-        uint64_t cb = A + 16ull * c;
-        uint32_t by[16];
+        const uint64_t cb = A + 16ull * c;
+        uint32_t u[4];
         if (vec_ok && cb + 16 <= n_bases) {
             uint4 v = __ldg(reinterpret_cast<const uint4 *>(reads + cb));
-            uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int q = 0; q < 16; q++) by[q] = (u[q >> 2] >> (8 * (q & 3))) & 0xFFu;
+            u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
         } else {
 #pragma unroll
-            for (int q = 0; q < 16; q++) by[q] = (cb + q >= start && cb + q < end) ? reads[cb + q] : 'A';
+            for (int q = 0; q < 4; q++) {
+                uint32_t x = 0;
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    uint64_t pos = cb + 4 * q + b;
+                    uint32_t by = (pos >= start && pos < end) ? reads[pos] : 'A';
+                    x |= by << (8 * b);
+                }
+                u[q] = x;
+            }
         }
         uint32_t c32 = 0;
 #pragma unroll
-        for (int q = 0; q < 16; q++) {
-            uint64_t pos = cb + q;
-            bool in = pos >= start && pos < end;
-            bool b = false;
-            uint32_t code = base_code(by[q], b);
-            if (in) { bad |= b; c32 |= code << (2 * q); }
+        for (int q = 0; q < 4; q++) {
+            int64_t wb = (int64_t)(cb + 4 * q);
+            uint32_t m = byte_mask((int64_t)start - wb, (int64_t)end - wb);
+            c32 |= swar_pack4(u[q], m, bad) << (8 * q);
         }
         int64_t j0 = (int64_t)cb - (int64_t)start;
         if (j0 < 0) { c32 >>= (uint32_t)(2 * (-j0)); j0 = 0; }
@@ -136,7 +164,62 @@ MT_DEV uint32_t lower_bound_u64(const uint64_t *a, uint32_t lo, uint32_t hi, uin
     return lo;
 }
 
-// warp bitonic sort of a[0, P), P a power of two >= 2
+// Bitonic sort of 32*R keys held in registers: element r*32 + lane in v[r]. Exchanges across
+// lanes use shuffles, exchanges across register slots stay in the lane.
+template <int R>
+MT_DEV void bitonic_regs(uint64_t (&v)[R]) {
+    const uint32_t lane = lane_id();
+    constexpr uint32_t P = 32u * R;
+#pragma unroll
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int pr = r ^ (int)(j >> 5);
+                    if (pr > r) {
+                        const uint32_t i = (uint32_t)r * 32u + lane;
+                        const bool up = (i & k) == 0;
+                        const uint64_t a = v[r], b = v[pr];
+                        const bool sw = (a > b) == up;
+                        v[r] = sw ? b : a;
+                        v[pr] = sw ? a : b;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const uint32_t i = (uint32_t)r * 32u + lane;
+                    const uint64_t o = __shfl_xor_sync(FULL, v[r], j);
+                    const bool up = (i & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    v[r] = (lower == up) ? (v[r] < o ? v[r] : o) : (v[r] < o ? o : v[r]);
+                }
+            }
+        }
+    }
+}
+
+template <int R>
+MT_DEV void sort_hits_R(uint64_t *h, uint32_t H) {
+    const uint32_t lane = lane_id();
+    uint64_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        uint32_t i = (uint32_t)r * 32u + lane;
+        v[r] = i < H ? h[i] : ~0ull;
+    }
+    bitonic_regs<R>(v);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        uint32_t i = (uint32_t)r * 32u + lane;
+        if (i < H) h[i] = v[r];
+    }
+    __syncwarp();
+}
+
+// warp bitonic sort of a[0, P) in shared memory, P a power of two >= 2
 MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
     const uint32_t lane = lane_id();
     for (uint32_t k = 2; k <= P; k <<= 1) {
@@ -151,6 +234,26 @@ MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
             __syncwarp();
         }
     }
+}
+
+// Up to 64 matches are sorted in registers; the rare larger sets in shared memory.
+MT_DEV void sort_hits(uint64_t *h, uint32_t H) {
+    if (H <= 32) sort_hits_R<1>(h, H);
+    else if (H <= 64) sort_hits_R<2>(h, H);
+    else {
+        uint32_t P = 128;
+        while (P < H) P <<= 1;
+        for (uint32_t i = H + lane_id(); i < P; i += 32) h[i] = ~0ull;
+        __syncwarp();
+        warp_bitonic(h, P);
+    }
+}
+
+MT_DEV void read_kmer_at(const uint64_t *rd, uint32_t p, uint32_t k, uint32_t canonical, uint64_t &code,
+                         uint32_t &strand) {
+    uint64_t fwd, rc;
+    kmer_codes(get32(rd, p), k, fwd, rc);
+    canon(fwd, rc, canonical, code, strand);
 }
 
 template <bool SMEM_HIST>
@@ -203,75 +306,150 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             const uint32_t tw = min(TILE, nwin - t0);
             const uint32_t npos = tw + w - 1;
             for (uint32_t i = lane; i < npos; i += 32) {
-                uint64_t x = get32(ws.rd, t0 + i);
-                uint64_t fwd, rc, c;
+                uint64_t c;
                 uint32_t st;
-                kmer_codes(x, k, fwd, rc);
-                canon(fwd, rc, canonical, c, st);
+                read_kmer_at(ws.rd, t0 + i, k, canonical, c, st);
                 ws.key[i] = mix64(c);
-                ws.code[i] = c | ((uint64_t)st << 63);
             }
             __syncwarp();
+            // (w,k)-minimizers: leftmost smallest key of each window, each position once.
+            // Lane l takes windows 4l..4l+3 of the tile; for w >= 4 the four windows share
+            // the k-mers [4l+3, 4l+w-1], so that minimum is found once.
             uint32_t nm = 0;
-            for (uint32_t rr = 0; rr * 32 < tw; rr++) {
-                uint32_t j = rr * 32 + lane;
-                int32_t sel = -1;
-                if (j < tw) {
-                    uint32_t b = j;
-                    uint64_t bk = ws.key[j];
-                    for (uint32_t t = 1; t < w; t++) {
-                        uint64_t kk = ws.key[j + t];
-                        if (kk < bk) { bk = kk; b = j + t; }
+            {
+                const uint32_t j0 = 4 * lane;
+                int32_t sel[4] = {-1, -1, -1, -1};
+                if (j0 < tw) {
+                    if (w >= 4) {
+                        uint32_t cp = j0 + 3;   // argmin of the shared part
+                        uint64_t ck = ws.key[cp];
+                        for (uint32_t t = j0 + 4; t < j0 + w; t++) {
+                            uint64_t kk = ws.key[t];
+                            if (kk < ck) { ck = kk; cp = t; }
+                        }
+                        // left parts [j0+a, j0+2] (a = 0..2), right parts [j0+w, j0+a+w-1] (a = 1..3)
+                        uint64_t k0 = ws.key[j0], k1 = ws.key[j0 + 1], k2 = ws.key[j0 + 2];
+                        uint64_t r0 = ws.key[j0 + w], r1 = ws.key[j0 + w + 1], r2 = ws.key[j0 + w + 2];
+                        uint32_t lp2 = j0 + 2; uint64_t lk2 = k2;
+                        uint32_t lp1 = (k1 <= lk2) ? j0 + 1 : lp2; uint64_t lk1 = (k1 <= lk2) ? k1 : lk2;
+                        uint32_t lp0 = (k0 <= lk1) ? j0 : lp1; uint64_t lk0 = (k0 <= lk1) ? k0 : lk1;
+                        uint32_t rp1 = j0 + w; uint64_t rk1 = r0;
+                        uint32_t rp2 = (r1 < rk1) ? j0 + w + 1 : rp1; uint64_t rk2 = (r1 < rk1) ? r1 : rk1;
+                        uint32_t rp3 = (r2 < rk2) ? j0 + w + 2 : rp2; uint64_t rk3 = (r2 < rk2) ? r2 : rk2;
+                        // window a = left part, shared part, right part, in position order
+                        uint32_t b0 = (lk0 <= ck) ? lp0 : cp; uint64_t bk0 = (lk0 <= ck) ? lk0 : ck;
+                        uint32_t b1 = (lk1 <= ck) ? lp1 : cp; uint64_t bk1 = (lk1 <= ck) ? lk1 : ck;
+                        b1 = (rk1 < bk1) ? rp1 : b1;
+                        uint32_t b2 = (lk2 <= ck) ? lp2 : cp; uint64_t bk2 = (lk2 <= ck) ? lk2 : ck;
+                        b2 = (rk2 < bk2) ? rp2 : b2;
+                        uint32_t b3 = (rk3 < ck) ? rp3 : cp;
+                        const uint32_t bb[4] = {b0, b1, b2, b3};
+#pragma unroll
+                        for (int a = 0; a < 4; a++)
+                            if (j0 + a < tw) sel[a] = (int32_t)(t0 + bb[a]);
+                    } else {
+#pragma unroll
+                        for (int a = 0; a < 4; a++) {
+                            const uint32_t j = j0 + a;
+                            if (j < tw) {
+                                uint32_t b = j;
+                                uint64_t bk = ws.key[j];
+                                for (uint32_t t = 1; t < w; t++) {
+                                    uint64_t kk = ws.key[j + t];
+                                    if (kk < bk) { bk = kk; b = j + t; }
+                                }
+                                sel[a] = (int32_t)(t0 + b);
+                            }
+                        }
                     }
-                    sel = (int32_t)(t0 + b);
                 }
-                int32_t prv = __shfl_up_sync(FULL, sel, 1);
+                int32_t prv = __shfl_up_sync(FULL, sel[3], 1);
                 if (lane == 0) prv = carry;
-                bool emit = (j < tw) && (sel != prv);
-                unsigned bal = __ballot_sync(FULL, emit);
-                if (emit) {
-                    uint32_t slot = nm + __popc(bal & ((1u << lane) - 1u));
-                    uint32_t li = (uint32_t)sel - t0;
-                    ws.mcode[slot] = ws.code[li];
-                    ws.mkey[slot] = ws.key[li];
-                    ws.mpos[slot] = (uint16_t)sel;
+                bool em[4];
+                uint32_t ne = 0;
+#pragma unroll
+                for (int a = 0; a < 4; a++) {
+                    em[a] = sel[a] >= 0 && sel[a] != prv;
+                    ne += em[a];
+                    if (sel[a] >= 0) prv = sel[a];
                 }
-                nm += __popc(bal);
-                uint32_t last = min(31u, tw - 1 - rr * 32);
-                carry = __shfl_sync(FULL, sel, last);
+                const uint32_t incl = warp_incl_scan(ne);
+                uint32_t o = nm + incl - ne;
+#pragma unroll
+                for (int a = 0; a < 4; a++)
+                    if (em[a]) ws.mpos[o++] = (uint16_t)sel[a];
+                nm += __shfl_sync(FULL, incl, 31);
+                // selection of the tile's last window, for the next tile
+                const uint32_t last_lane = (tw - 1) / 4;
+                int32_t lastsel = sel[0];
+#pragma unroll
+                for (int a = 1; a < 4; a++) if (((tw - 1) & 3) == (uint32_t)a) lastsel = sel[a];
+                carry = __shfl_sync(FULL, lastsel, last_lane);
             }
             __syncwarp();
             n_mins += nm;
+            // index lookups, 32 at a time, then a cooperative gather of all their matches
             for (uint32_t m0 = 0; m0 < nm; m0 += 32) {
                 const uint32_t m = m0 + lane;
-                Lookup L;
-                L.cnt = 0; L.ninline = 0; L.off = 0;
-                uint32_t cnt = 0, rpos = 0, rst = 0;
+                uint32_t cnt = 0;
                 if (m < nm) {
-                    uint64_t cs = ws.mcode[m];
-                    rst = (uint32_t)(cs >> 63);
-                    rpos = ws.mpos[m];
-                    L = probe(A.ix, cs & CODE_MASK62, ws.mkey[m], &A.ctr->err);
-                    cnt = L.cnt <= A.max_occ ? L.cnt : 0;
-                    if (!L.ninline) n_ext += cnt;
+                    const uint32_t p = ws.mpos[m];
+                    uint64_t code;
+                    uint32_t st;
+                    read_kmer_at(ws.rd, p, k, canonical, code, st);
+                    const uint64_t key = ws.key[p - t0];
+                    uint64_t s = slot_of(key, A.ix.slot_shift);
+                    const uint64_t want = code + 1;
+                    uint32_t ni = 0;
+                    uint64_t w1 = 0;
+                    for (uint64_t it = 0; it <= A.ix.slot_mask; it++) {
+                        const ulonglong2 a = __ldg(&A.ix.table[2 * s]);
+                        if (a.x == 0) break;
+                        if ((a.x & CODE_MASK62) == want) {
+                            ni = (uint32_t)(a.x >> 62);
+                            w1 = a.y;
+                            cnt = ni ? ni : (uint32_t)(a.y >> 40);
+                            if (ni > 1) {
+                                const ulonglong2 b2 = __ldg(&A.ix.table[2 * s + 1]);
+                                ws.inl[lane * 3 + 1] = b2.x;
+                                ws.inl[lane * 3 + 2] = b2.y;
+                            }
+                            break;
+                        }
+                        s = (s + 1) & A.ix.slot_mask;
+                    }
+                    if (cnt > A.max_occ) cnt = 0;
+                    ws.inl[lane * 3] = w1;
+                    ws.off[lane] = w1 & OFF_MASK40;
+                    ws.meta[lane] = p | (st << 16) | (ni << 17);
+                    if (!ni) n_ext += cnt;
                 }
-                uint32_t incl = warp_incl_scan(cnt);
-                uint32_t total = __shfl_sync(FULL, incl, 31);
-                uint32_t excl = incl - cnt;
+                const uint32_t incl = warp_incl_scan(cnt);
+                const uint32_t total = __shfl_sync(FULL, incl, 31);
+                ws.pref[lane] = incl - cnt;
+                if (lane == 31) ws.pref[32] = incl;
                 if (!ovf && H + total > HCAP) {
                     // switch to counting only: count what is buffered so far
                     for (uint32_t i = lane; i < H; i += 32) atomicAdd(&H_out[hk_genome(ws.hits[i])], 1ull);
                     ovf = true;
                 }
-                if (!ovf) {
-                    for (uint32_t t = 0; t < cnt; t++)
-                        ws.hits[H + excl + t] = hit_key(occ_at(A.ix, L, t), rpos, rst, n, k);
-                } else {
-                    for (uint32_t t = 0; t < cnt; t++) atomicAdd(&H_out[occ_at(A.ix, L, t) >> 33], 1ull);
+                __syncwarp();
+                const uint32_t nl = min(32u, nm - m0);
+                for (uint32_t q = lane; q < total; q += 32) {
+                    uint32_t lo = 0, hi = nl;   // owner: last lookup with pref <= q
+                    while (hi - lo > 1) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (ws.pref[mid] <= q) lo = mid; else hi = mid;
+                    }
+                    const uint32_t t = q - ws.pref[lo];
+                    const uint32_t meta = ws.meta[lo];
+                    const uint64_t occ = (meta >> 17) ? ws.inl[lo * 3 + t] : __ldg(&A.ix.occ[ws.off[lo] + t]);
+                    if (!ovf) ws.hits[H + q] = hit_key(occ, meta & 0xFFFFu, (meta >> 16) & 1u, n, k);
+                    else atomicAdd(&H_out[occ >> 33], 1ull);
                 }
                 H += total;
+                __syncwarp();
             }
-            __syncwarp();
         }
         n_hits += H;
         if (ovf) {
@@ -286,44 +464,44 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             if (lane == 0) A.qcnt[r] = 0;
             continue;
         }
-        uint32_t P = 2;
-        while (P < H) P <<= 1;
-        for (uint32_t i = H + lane; i < P; i += 32) ws.hits[i] = ~0ull;
-        __syncwarp();
-        warp_bitonic(ws.hits, P);
-        // containment counts, one atomic per genome run
-        for (uint32_t i = lane; i < H; i += 32) {
-            uint32_t g = hk_genome(ws.hits[i]);
-            if (i == 0 || hk_genome(ws.hits[i - 1]) != g) {
-                uint32_t e = lower_bound_u64(ws.hits, i + 1, H, ((uint64_t)g + 1) << 34);
-                atomicAdd(&H_out[g], (unsigned long long)(e - i));
-            }
+        sort_hits(ws.hits, H);
+        // (genome, strand) groups of the sorted matches, in order
+        uint32_t ng = 0;
+        for (uint32_t i0 = 0; i0 < H; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            const bool st = i < H && (i == 0 || (ws.hits[i] >> 33) != (ws.hits[i - 1] >> 33));
+            const unsigned bal = __ballot_sync(FULL, st);
+            if (st) ws.gs[ng + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)i;
+            ng += __popc(bal);
         }
-        // greedy locations: a location starting at match i ends before the first match
-        // with key >= key_i + E + 1 (a later diagonal band, strand or genome)
-        for (uint32_t i = lane; i < H; i += 32)
-            ws.nxt[i] = (uint16_t)lower_bound_u64(ws.hits, i + 1, H, ws.hits[i] + E + 1);
+        if (lane == 0) { ws.gs[ng] = (uint16_t)H; ws.qcount = 0; }
         __syncwarp();
-        uint32_t Q = 0;
-        if (lane == 0) {
-            uint32_t s = 0;
-            while (s < H) {
-                uint32_t e = ws.nxt[s];
-                if (e - s >= A.min_seeds) ws.qs[Q++] = (uint16_t)s;
+        // containment counts (one atomic per group) and greedy locations per group: a
+        // location starting at match s ends before the first match with key >= key_s + E + 1
+        for (uint32_t gi = lane; gi < ng; gi += 32) {
+            uint32_t s = ws.gs[gi];
+            const uint32_t ge = ws.gs[gi + 1];
+            atomicAdd(&H_out[hk_genome(ws.hits[s])], (unsigned long long)(ge - s));
+            while (s < ge) {
+                const uint32_t e = lower_bound_u64(ws.hits, s + 1, ge, ws.hits[s] + E + 1);
+                if (e - s >= A.min_seeds) {
+                    const uint32_t qi = atomicAdd(&ws.qcount, 1u);
+                    ws.qs[qi] = (uint16_t)s;
+                    ws.qn[qi] = (uint16_t)(e - s);
+                }
                 s = e;
             }
         }
-        Q = __shfl_sync(FULL, Q, 0);
         __syncwarp();
+        const uint32_t Q = ws.qcount;
+        // rank the qualifying locations: seeds descending, then (genome, strand, diagonal)
         for (uint32_t qi = lane; qi < Q; qi += 32) {
-            uint32_t si = ws.qs[qi];
-            uint32_t seeds_i = ws.nxt[si] - si;
-            uint64_t hk_i = ws.hits[si];
+            const uint32_t seeds_i = ws.qn[qi];
+            const uint64_t hk_i = ws.hits[ws.qs[qi]];
             uint32_t rank = 0;
             for (uint32_t qj = 0; qj < Q; qj++) {
-                uint32_t sj = ws.qs[qj];
-                uint32_t seeds_j = ws.nxt[sj] - sj;
-                uint64_t hk_j = ws.hits[sj];
+                const uint32_t seeds_j = ws.qn[qj];
+                const uint64_t hk_j = ws.hits[ws.qs[qj]];
                 rank += (seeds_j > seeds_i) || (seeds_j == seeds_i && hk_j < hk_i);
             }
             if (rank < CSTORE) {
