@@ -30,6 +30,11 @@ sys.path.insert(0, ROOT)
 import gen  # noqa: E402
 
 METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact); p50/p99"
+# DRAM bytes (read + write) per read of the seeding kernel, from one ncu capture of the current
+# kernel on 2e6 reads of the same workload (dram__bytes_read.sum + dram__bytes_write.sum =
+# 7.485e9 bytes); the index is fixed, so traffic grows in proportion to the reads. Set to None
+# whenever the kernel changes until it is captured again.
+SEED_DRAM_BYTES_PER_READ = 7.485e9 / 2e6
 WORKLOAD = ("medium: 200 genomes x 2 Mb (20 clades x 10, 1-10% divergence), k21 w11 canonical, "
             "1e7 reads x 150 bp (both strands, 0.5% subst + 0.05% indel, 5% random), E=8, min_seeds 3, top 3")
 
@@ -357,7 +362,8 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     achieved = seed_bytes / (st["ms_seed"] / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": args.seed_traffic, "kernel": "k_seed",
+                "traffic": (SEED_DRAM_BYTES_PER_READ * n_reads if SEED_DRAM_BYTES_PER_READ else None),
+                "kernel": "k_seed",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": seed_bytes, "ms_per_launch": st["ms_seed"],
                 "stage_ms": {k[3:]: st[k] for k in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")}}
@@ -422,8 +428,6 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--ref-sample", type=int, default=20_000)
-    ap.add_argument("--seed-traffic", type=float, default=None,
-                    help="ncu dram bytes per seeding launch, scaled to the full batch")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

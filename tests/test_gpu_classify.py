@@ -79,6 +79,19 @@ def clade(mt):
     return c, g, r, ix, oix
 
 
+def test_clade_workload_warp_path_only(mt):
+    """The clade workload with w = 9: no thread-per-read kernel for it, every read is seeded by
+    the warp-per-read kernel."""
+    c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=5_000, w=9)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    prm = _params(c)
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=8)
+    compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_clade_workload(mt, clade, mode):
     c, g, r, ix, oix = clade
@@ -102,9 +115,12 @@ def test_clade_parameter_sweep(mt, clade, kw):
     compare_classify(out, ref)
 
 
-def test_mixed_lengths_and_edges(mt):
+@pytest.mark.parametrize("kw", [(15, 10), (13, 7), (21, 11)])
+def test_mixed_lengths_and_edges(mt, kw):
     """Reads of 1..1024 bases (below k+w-1, exactly MT_MAX_READ_LEN), reads overhanging genome
-    ends on both strands, E from a per-mille threshold."""
+    ends on both strands, E from a per-mille threshold. w = 10 and 11 take the thread-per-read
+    seeding path (long reads handed to the warp kernel); w = 7 runs the warp kernel only."""
+    k, w = kw
     rng = np.random.default_rng(5)
     gs = [gen.ascii_of(rng.integers(0, 4, L, dtype=np.uint8)) for L in (3000, 1500, 5000)]
     gseq = np.concatenate(gs)
@@ -128,8 +144,8 @@ def test_mixed_lengths_and_edges(mt):
         reads.append(s)
     rseq = np.concatenate(reads)
     roff = np.cumsum([0] + [len(x) for x in reads]).astype(np.uint64)
-    ix = mt.Index(gseq, goff, 15, 10, 1)
-    oix = oracle.Index(gseq, goff, 15, 10, 1)
+    ix = mt.Index(gseq, goff, k, w, 1)
+    oix = oracle.Index(gseq, goff, k, w, 1)
     for prm in (dict(e_abs=0, e_permille=60, min_seeds=2), dict(e_abs=5, e_permille=0, min_seeds=1, top_n=5)):
         p = _params(dict(e_abs=0, e_permille=0, min_seeds=2), **prm)
         ref = oracle.classify(oix, rseq, roff, oracle_params(p))
