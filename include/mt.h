@@ -188,6 +188,25 @@ int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off, uint64_t 
                  const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
                  const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist);
 
+/* ---- the same stage without any device allocation ----------------------------------------
+ * No counterpart in the paper: an addition for callers that cannot allocate device memory
+ * during a call (a serving loop with a fixed device footprint, a host framework that owns the
+ * allocator, code that must not grow its footprint after start-up). Identical arguments,
+ * layouts, limits and results as mt_eda_batch (all pointers DEVICE pointers), except:
+ *  - its scratch is a fixed array of ~4 MiB in the library, one per device that loads the
+ *    library, held until the process exits; n_pairs above 2^20 fails with MT_EINVAL;
+ *  - the first call on a device looks up that array's device address (once per device, with
+ *    the device current); make that first call before any stream capture;
+ *  - every call uses the same array, so calls whose work overlaps on the GPU (other threads or
+ *    streams) race and must be serialised by the caller;
+ *  - the batched form uses lanes per pair already tuned in this process, else a default; it
+ *    times nothing itself.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. Returns after synchronising
+ * `stream`. Errors: MT_EINVAL, MT_ECUDA. */
+int mt_eda_batch_noalloc(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
+                         const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
+                         const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist);
+
 /* ---- continuous-batching serving loop over one resident index --------------------------
  * Requests (read batches) are admitted while a slot is free and their workspace fits in
  * hbm_budget bytes; admitted requests run concurrently on their own streams. Inputs are

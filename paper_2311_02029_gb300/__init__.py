@@ -70,7 +70,7 @@ class IndexInfo(ctypes.Structure):
 
 EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
            "mt_index_get_info", "mt_classify", "mt_classify_workspace_bytes", "mt_pack_seqs",
-           "mt_eda_batch", "mt_server_create", "mt_server_submit", "mt_server_poll",
+           "mt_eda_batch", "mt_eda_batch_noalloc", "mt_server_create", "mt_server_submit", "mt_server_poll",
            "mt_server_cancel", "mt_server_destroy"]
 
 
@@ -101,6 +101,8 @@ def lib():
         L.mt_pack_seqs.argtypes = [vp, vp, u64, vp, vp]
         L.mt_eda_batch.restype = i32
         L.mt_eda_batch.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp]
+        L.mt_eda_batch_noalloc.restype = i32
+        L.mt_eda_batch_noalloc.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp]
         L.mt_server_create.restype = i32
         L.mt_server_create.argtypes = [vp, u64, i32, ctypes.POINTER(ClassifyParams), ctypes.POINTER(vp)]
         L.mt_server_submit.restype = i32
@@ -278,6 +280,20 @@ def eda_batch(read_words, read_off, win_words, win_off, pair_read, E, mode=MT_ED
     _check(lib().mt_eda_batch(_ptr(read_words), _ptr(read_off), read_off.numel() - 1, _ptr(win_words),
                               _ptr(win_off), _ptr(pair_read), _ptr(E), n_pairs, mode, _stream(stream),
                               _ptr(dist)), "mt_eda_batch")
+    return dist
+
+
+NOALLOC_MAX_PAIRS = 1 << 20
+
+
+def eda_batch_noalloc(read_words, read_off, win_words, win_off, pair_read, E, dist, mode=MT_EDA_BATCHED,
+                      stream=None):
+    """``mt_eda_batch_noalloc`` on CUDA tensors into a caller-provided uint8 ``dist``. For
+    callers that cannot allocate device memory during a call; the library uses a fixed
+    per-device array instead, so at most 2^20 pairs per call and calls must not overlap."""
+    _check(lib().mt_eda_batch_noalloc(_ptr(read_words), _ptr(read_off), read_off.numel() - 1, _ptr(win_words),
+                                      _ptr(win_off), _ptr(pair_read), _ptr(E), pair_read.numel(), mode,
+                                      _stream(stream), _ptr(dist)), "mt_eda_batch_noalloc")
     return dist
 
 

@@ -502,3 +502,117 @@ extern "C" int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off
     if (!cuda_ok(e, "mt_eda_batch")) return MT_ECUDA;
     return MT_OK;
 }
+
+namespace mt {
+// ---- allocation-free variant of the batch call ----------------------------------------------
+// Some callers cannot allocate device memory during a call: code that runs where
+// cudaMalloc / cudaMallocAsync are not permitted or would stall the pipeline (inside a
+// latency-critical serving loop with a fixed memory footprint, under an allocator owned by a
+// host framework that forbids side allocations, or in processes that must not grow their
+// device footprint after start-up). For them, mt_eda_batch_noalloc keeps its scratch (bucket
+// statistics, cursors, the pair permutation) in the fixed array below instead of allocating.
+static constexpr uint64_t NOALLOC_MAX_PAIRS = 1ull << 20;   // 4 MiB of permutation
+
+struct NoAllocScratch {
+    BucketStats st;
+    unsigned long long cursor[64];
+    uint32_t perm[NOALLOC_MAX_PAIRS];
+};
+
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+static std::mutex g_noalloc_mu;
+static NoAllocScratch *g_noalloc_ptr[64] = {nullptr};
+
+// The device address of the array for the current device. The host symbol is only a
+// stand-in, so the address is asked from the runtime once per device (with that device
+// current) and cached.
+static int noalloc_scratch(NoAllocScratch **out) {
+    int dev = 0;
+    MT_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return MT_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (!cuda_ok(e, "cudaGetSymbolAddress(g_noalloc_scratch)")) return MT_ECUDA;
+        g_noalloc_ptr[dev] = reinterpret_cast<NoAllocScratch *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return MT_OK;
+}
+}  // namespace mt
+
+extern "C" int mt_eda_batch_noalloc(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
+                                    const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
+                                    const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist) {
+    if (mode != MT_EDA_BATCHED && mode != MT_EDA_PLAIN) return MT_EINVAL;
+    if (n_pairs > NOALLOC_MAX_PAIRS) return MT_EINVAL;
+    if (n_pairs == 0) return MT_OK;
+    if (!read_words || !read_off || !win_words || !win_off || !pair_read || !E || !dist || n_reads == 0)
+        return MT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    NoAllocScratch *sc = nullptr;
+    int rc = noalloc_scratch(&sc);
+    if (rc) return rc;
+    BucketStats *st = &sc->st;
+    unsigned long long *cursor = sc->cursor;
+    uint32_t *perm = sc->perm;
+    // the array keeps the previous call's contents: clear the counters that must start at 0
+    MT_CK(cudaMemsetAsync(st, 0, sizeof(BucketStats), s));
+    {
+        unsigned blocks = (unsigned)std::min<uint64_t>((n_pairs + 255) / 256, (uint64_t)sm_count() * 8);
+        k_bucket_count<<<blocks, 256, 0, s>>>(read_off, n_reads, win_off, pair_read, E, n_pairs, st);
+        MT_CK(cudaGetLastError());
+    }
+    BucketStats h{};
+    MT_CK(cudaMemcpyAsync(&h, st, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    if (h.err) return MT_EINVAL;
+    BatchSrc src;
+    src.rw = read_words; src.roff = read_off; src.ww = win_words; src.woff = win_off;
+    src.pair_read = pair_read; src.E = E; src.dist = dist;
+    const int by_class = mode == MT_EDA_BATCHED;
+    const int nkeys = by_class ? MAX_CLASSES : 33;
+    unsigned long long start[34] = {0};
+    for (int i = 0; i < nkeys; i++) start[i + 1] = start[i] + (by_class ? h.cls_count[i] : h.bkt_count[i]);
+    MT_CK(cudaMemcpyAsync(cursor, start, nkeys * 8, cudaMemcpyHostToDevice, s));
+    {
+        unsigned blocks = (unsigned)std::min<uint64_t>((n_pairs + 255) / 256, (uint64_t)sm_count() * 8);
+        k_bucket_scatter<<<blocks, 256, 0, s>>>(read_off, pair_read, E, n_pairs, by_class, cursor, perm);
+        MT_CK(cudaGetLastError());
+    }
+    unsigned long long *counter = cursor + 48;
+    if (mode == MT_EDA_PLAIN) {
+        for (int b = 1; b <= 32; b++) {
+            if (!h.bkt_count[b]) continue;
+            uint32_t maxn = (uint32_t)b * 32;
+            rc = launch_plain(src, perm, start[b], start[b + 1], nullptr, eda_read_words(maxn),
+                              eda_win_words(maxn, h.bkt_maxE[b]), s);
+            if (rc) return rc;
+        }
+    } else {
+        // lanes per pair: the autotuned value when this process has one, else the default
+        // (no timing runs here, so no events are created)
+        int dev = 0;
+        cudaGetDevice(&dev);
+        EdaPlan plan{};
+        uint32_t minG = 32;
+        for (int c = 0; c < MAX_CLASSES; c++) {
+            if (!h.cls_count[c]) continue;
+            uint32_t G = 0;
+            if (!tuned_G(dev, c, &G)) G = default_G(h.cls_maxE[c]);
+            uint32_t k = plan.n_classes++;
+            plan.G[k] = G;
+            plan.begin[k] = start[c];
+            plan.end[k] = start[c + 1];
+            minG = std::min(minG, G);
+        }
+        plan.groups_max = 32 / minG;
+        rc = launch_persistent(src, perm, plan, counter, eda_read_words(h.maxn), eda_win_words(h.maxn, h.maxE), s);
+        if (rc) return rc;
+    }
+    MT_CK(cudaStreamSynchronize(s));
+    return MT_OK;
+}
