@@ -125,6 +125,7 @@ struct EdaPlan {
     uint32_t G[MAX_CLASSES];
     uint64_t begin[MAX_CLASSES], end[MAX_CLASSES];
     const uint64_t *dyn_end;           // if set: class 0 ends at *dyn_end (device count)
+    uint64_t cap;                      // if set: class 0 holds at most `cap` items (tuning samples)
 };
 
 template <int G, class Src>
@@ -157,8 +158,10 @@ __global__ void __launch_bounds__(EDA_THREADS) k_eda_persistent(Src src, const u
     // chunk table: chunks of 128 items per class
     uint64_t pref[MAX_CLASSES + 1];
     pref[0] = 0;
+    uint64_t end0 = plan.dyn_end ? *plan.dyn_end : plan.end[0];
+    if (plan.cap && end0 > plan.begin[0] + plan.cap) end0 = plan.begin[0] + plan.cap;
     for (uint32_t c = 0; c < plan.n_classes; c++) {
-        uint64_t e = (c == 0 && plan.dyn_end) ? *plan.dyn_end : plan.end[c];
+        uint64_t e = c == 0 ? end0 : plan.end[c];
         uint64_t cnt = e > plan.begin[c] ? e - plan.begin[c] : 0;
         pref[c + 1] = pref[c] + (cnt + 127) / 128;
     }
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(EDA_THREADS) k_eda_persistent(Src src, const u
         if (id >= total) break;
         uint32_t c = 0;
         while (id >= pref[c + 1]) c++;
-        uint64_t e = (c == 0 && plan.dyn_end) ? *plan.dyn_end : plan.end[c];
+        uint64_t e = c == 0 ? end0 : plan.end[c];
         uint64_t b = plan.begin[c] + (id - pref[c]) * 128;
         uint64_t ee = b + 128 < e ? b + 128 : e;
         switch (plan.G[c]) {
@@ -324,7 +327,7 @@ static int launch_plain(const Src &src, const uint32_t *perm, uint64_t begin, ui
 // sample of the class the first time the class is seen in this process (per device).
 struct TuneCache {
     std::mutex mu;
-    int G[64][MAX_CLASSES];   // per device; 0 = not tuned
+    int G[64][2 * MAX_CLASSES];   // per device: EDA-only classes, then classification classes
     TuneCache() { memset(G, 0, sizeof(G)); }
 };
 static TuneCache g_tune;
@@ -398,10 +401,35 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const uint64_t 
         return launch_plain(src, nullptr, 0, max_items, cl_count, rww, www, s);
     int dev = 0;
     cudaGetDevice(&dev);
-    uint32_t cls = e_class(maxE);
+    const uint32_t slot = MAX_CLASSES + e_class(maxE);
     uint32_t G = 0;
-    if (!tuned_G(dev, 7, &G)) G = default_G(maxE);   // slot 7 unused by E <= 127 classes of classify
-    (void)cls;
+    if (!tuned_G(dev, slot, &G)) {
+        // time every lanes-per-pair choice on the first 2^17 candidates of this call
+        cudaEvent_t e0, e1;
+        MT_CK(cudaEventCreate(&e0));
+        MT_CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        G = default_G(maxE);
+        for (int rep = 0; rep < 2; rep++) {
+            for (uint32_t g : {1u, 2u, 4u, 8u, 16u, 32u}) {
+                EdaPlan tp{};
+                tp.n_classes = 1; tp.G[0] = g; tp.groups_max = 32 / g;
+                tp.begin[0] = 0; tp.end[0] = max_items; tp.dyn_end = cl_count; tp.cap = 1ull << 17;
+                if (eda_smem(tp.groups_max, rww, www) > 96 * 1024) continue;
+                MT_CK(cudaEventRecord(e0, s));
+                int rc = launch_persistent(src, nullptr, tp, counter, rww, www, s);
+                if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+                MT_CK(cudaEventRecord(e1, s));
+                MT_CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                MT_CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep == 1 && ms < best) { best = ms; G = g; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_tuned_G(dev, slot, G);
+    }
     EdaPlan plan{};
     plan.n_classes = 1;
     plan.G[0] = G;

@@ -40,16 +40,40 @@ MT_DEV uint32_t next_mismatch(const uint64_t *rd, const uint64_t *wn, uint32_t n
 }
 
 // The walk for one pair, executed by the G lanes of `gmask` (glane = lane within group).
+// Lane glane owns the contiguous diagonal range [glane*T, glane*T + T), T = ceil((2E+1)/G).
+// Per step it loads the read's 32 columns from c once and the window's bases from c + its
+// first diagonal (up to 32 + T bases) once; each diagonal's 32 columns then come from a
+// register funnel shift. Only a diagonal whose first 32 columns all match walks on further.
 template <int G, bool EDGES>
 MT_DEV uint32_t sneaky_walk(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E,
                             int32_t lo, int32_t hi, unsigned gmask, uint32_t glane) {
     const uint32_t ndiag = 2 * E + 1;
+    const uint32_t T = (ndiag + G - 1) / G;
+    const uint32_t d0 = glane * T;
+    const uint32_t d1 = min(d0 + T, ndiag);
     uint32_t c = 0, cnt = 0;
     while (c < n) {
         uint32_t best = c;
-        for (uint32_t di = glane; di < ndiag; di += G) {
-            uint32_t m = next_mismatch<EDGES>(rd, wn, n, c, di, lo, hi);
-            best = m > best ? m : best;
+        if (d0 < d1) {
+            const uint64_t r0 = get32(rd, c);
+            for (uint32_t tb = d0; tb < d1; tb += 32) {   // blocks of 32 diagonals
+                const uint32_t q = c + tb;
+                const uint64_t w0 = get32(wn, q);
+                const uint64_t w1 = get32(wn, q + 32);
+                const uint32_t tn = min(32u, d1 - tb);
+                for (uint32_t t = 0; t < tn; t++) {
+                    const uint32_t sh = 2 * t;
+                    const uint64_t x = t ? ((w0 >> sh) | (w1 << (64 - sh))) : w0;
+                    const uint64_t y = r0 ^ x;
+                    uint64_t m = (y | (y >> 1)) & EVEN_BITS;
+                    if (EDGES) m |= edge_mask((int32_t)(q + t), lo, hi);
+                    uint32_t e;
+                    if (m) e = c + ((uint32_t)(__ffsll((long long)m) - 1) >> 1);
+                    else e = next_mismatch<EDGES>(rd, wn, n, c + 32, tb + t, lo, hi);
+                    e = e < n ? e : n;
+                    best = e > best ? e : best;
+                }
+            }
         }
         if (G > 1) best = __reduce_max_sync(gmask, best);
         c = best;
