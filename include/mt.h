@@ -49,6 +49,7 @@ extern "C" {
 
 typedef struct mt_index mt_index;     /* opaque device-resident reference index */
 typedef struct mt_server mt_server;   /* opaque continuous-batching request loop */
+typedef struct mt_plan mt_plan;       /* opaque preallocated classification with a CUDA graph */
 
 /* Index parameters (Results, "Evaluation Methodology": minimap2 short-read seeds; the
  * paper's containment index uses k = 28, w = 18; the workloads here use k15/w10, k21/w11). */
@@ -104,6 +105,7 @@ typedef struct {
     double ms_eda;           /* edit-distance approximation */
     double ms_profile;       /* per-read decision, multi-read split, abundances */
     double ms_total;         /* first to last kernel of the call */
+    uint64_t err_bits;       /* device-side error flags of the call (0 when it succeeded) */
 } mt_stats;
 
 typedef struct {
@@ -153,7 +155,8 @@ int mt_index_get_info(const mt_index *ix, mt_index_info *info);
  * device_ptrs: 1 = reads, offsets and every output pointer are device pointers (the call
  *   still synchronises `stream` before returning, to report input errors); 0 = all are
  *   host pointers (copies are made on `stream`).
- * Outputs (any may be NULL except taxon): taxon[n_reads] (genome or -1);
+ * Outputs (any may be NULL except taxon, which may be NULL only when n_reads is 0):
+ *   taxon[n_reads] (genome or -1);
  *   nloc[n_reads]; locs[n_reads * top_n] (unused slots have genome -1);
  *   genome_hits[n_genomes] (stage-1 counts); abundance[n_genomes]; stats.
  * Errors: MT_EINVAL (bad base, read longer than MT_MAX_READ_LEN, bad offsets, parameter
@@ -162,6 +165,25 @@ int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
                 const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
                 int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
                 uint64_t *genome_hits, double *abundance, mt_stats *stats);
+
+/* ---- batched form with a captured CUDA graph ---------------------------------------------
+ * A plan holds a preallocated workspace sized for batches of up to max_reads reads,
+ * max_bases bases and reads of at most max_read_len bases, and the classification kernels
+ * captured once into a CUDA graph. Every kernel reads the batch's pointers and sizes from a
+ * small device block written per call, so the same graph serves every batch up to the
+ * capacity: the first mt_plan_classify runs the kernels directly (and may autotune the
+ * approximation), the second captures them on `stream` and every call after that replays the
+ * graph. Results are identical to mt_classify with the same parameters.
+ * Arguments of mt_plan_classify are those of mt_classify; batches above the capacity or with
+ * a longer read fail with MT_EINVAL. A plan is used by one thread at a time. */
+int mt_plan_create(const mt_index *ix, const mt_classify_params *params, uint64_t max_reads,
+                   uint64_t max_bases, uint32_t max_read_len, mt_plan **out);
+int mt_plan_classify(mt_plan *plan, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                     uint64_t n_reads, int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc,
+                     mt_loc *locs, uint64_t *genome_hits, double *abundance, mt_stats *stats);
+/* Device bytes held by the plan (its workspace). */
+uint64_t mt_plan_device_bytes(const mt_plan *plan);
+void mt_plan_destroy(mt_plan *plan);
 
 /* Device bytes of scratch that one mt_classify call needs for this batch shape
  * (inputs and outputs not included). Used for admission control. */

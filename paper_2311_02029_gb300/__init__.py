@@ -54,7 +54,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("n_reads", "n_minimizers", "n_hits", "n_candidates", "n_accepted", "n_multi",
                  "n_fallback", "workspace_bytes", "n_ext_occ", "n_stored", "n_launches")] + \
-               [(n, ctypes.c_double) for n in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")]
+               [(n, ctypes.c_double) for n in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")] + \
+               [("err_bits", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if n.startswith("ms_") else int(getattr(self, n)))
@@ -70,7 +71,8 @@ class IndexInfo(ctypes.Structure):
 
 EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
            "mt_index_get_info", "mt_classify", "mt_classify_workspace_bytes", "mt_pack_seqs",
-           "mt_eda_batch", "mt_eda_batch_noalloc", "mt_server_create", "mt_server_submit", "mt_server_poll",
+           "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
+           "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
            "mt_server_cancel", "mt_server_destroy"]
 
 
@@ -103,6 +105,13 @@ def lib():
         L.mt_eda_batch.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp]
         L.mt_eda_batch_noalloc.restype = i32
         L.mt_eda_batch_noalloc.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp]
+        L.mt_plan_create.restype = i32
+        L.mt_plan_create.argtypes = [vp, ctypes.POINTER(ClassifyParams), u64, u64, u32, ctypes.POINTER(vp)]
+        L.mt_plan_classify.restype = i32
+        L.mt_plan_classify.argtypes = [vp, vp, u64, vp, u64, i32, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.mt_plan_device_bytes.restype = u64
+        L.mt_plan_device_bytes.argtypes = [vp]
+        L.mt_plan_destroy.argtypes = [vp]
         L.mt_server_create.restype = i32
         L.mt_server_create.argtypes = [vp, u64, i32, ctypes.POINTER(ClassifyParams), ctypes.POINTER(vp)]
         L.mt_server_submit.restype = i32
@@ -244,6 +253,66 @@ def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None
     _check(rc, "mt_classify")
     out["stats"] = st.as_dict()
     return out
+
+
+class Plan:
+    """Preallocated classification replayed from a captured CUDA graph (``mt_plan_*``)."""
+
+    def __init__(self, ix: Index, max_reads: int, max_bases: int, max_read_len: int = 256, **params):
+        self.ix = ix
+        self.p = classify_params(**params)
+        h = ctypes.c_void_p()
+        _check(lib().mt_plan_create(ix.handle, ctypes.byref(self.p), max_reads, max_bases, max_read_len,
+                                    ctypes.byref(h)), "mt_plan_create")
+        self._h = h
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().mt_plan_device_bytes(self._h))
+
+    def classify(self, reads, offsets, *, stream=None, want_locs=True, out=None) -> dict:
+        st = Stats()
+        G = self.ix.n_genomes
+        tn = self.p.top_n
+        if _is_torch(reads) and reads.is_cuda:
+            import torch
+            dev = reads.device
+            n_reads = offsets.numel() - 1
+            out = dict(taxon=torch.empty(n_reads, dtype=torch.int32, device=dev),
+                       nloc=torch.empty(n_reads, dtype=torch.uint8, device=dev),
+                       locs=torch.empty((n_reads, tn, 24), dtype=torch.uint8, device=dev) if want_locs else None,
+                       genome_hits=torch.empty(G, dtype=torch.int64, device=dev),
+                       abundance=torch.empty(G, dtype=torch.float64, device=dev))
+            rc = lib().mt_plan_classify(self._h, _ptr(reads), reads.numel(), _ptr(offsets), n_reads, 1, _stream(stream),
+                                        _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                        _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+        else:
+            r = _host_u8(reads)
+            off = _host_u64(offsets)
+            n_reads = len(off) - 1
+            if out is None:
+                out = dict(taxon=np.empty(n_reads, np.int32), nloc=np.empty(n_reads, np.uint8),
+                           locs=np.empty((n_reads, tn), LOC_DTYPE) if want_locs else None,
+                           genome_hits=np.empty(G, np.uint64), abundance=np.empty(G, np.float64))
+            else:
+                out = dict(out)
+            rc = lib().mt_plan_classify(self._h, _ptr(r), len(r), _ptr(off), n_reads, 0, _stream(stream),
+                                        _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                        _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+        _check(rc, "mt_plan_classify")
+        out["stats"] = st.as_dict()
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mt_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def locs_from_device(t) -> np.ndarray:

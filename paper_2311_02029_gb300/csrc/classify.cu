@@ -25,11 +25,11 @@
 #include "internal.h"
 
 namespace mt {
-int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const uint64_t *roff, uint64_t off0,
+int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *io,
                         const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
                         const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
                         uint32_t maxn, uint32_t maxE, uint32_t mode, uint8_t *dist,
-                        unsigned long long *counter, cudaStream_t s);
+                        unsigned long long *counter, cudaStream_t s, bool allow_tune);
 
 static constexpr unsigned FULL = 0xffffffffu;
 static constexpr int SEED_WARPS = 8;
@@ -74,12 +74,7 @@ struct Counters {
 
 struct SeedArgs {
     IndexView ix;
-    const uint8_t *reads;
-    uint64_t n_bases;
-    const uint64_t *roff;
-    uint64_t n_reads;
-    uint64_t off0;
-    int vec_ok;
+    const IoBlock *io;
     uint32_t e_abs, e_permille, min_seeds, max_occ;
     uint64_t *rw;
     uint32_t *qcnt;
@@ -272,25 +267,26 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
     const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
     unsigned long long n_mins = 0, n_hits = 0, n_ext = 0, n_stored = 0;
 
+    const IoBlock io = *A.io;
     const uint64_t total_warps = (uint64_t)gridDim.x * SEED_WARPS;
-    for (uint64_t r = (uint64_t)blockIdx.x * SEED_WARPS + warp; r < A.n_reads; r += total_warps) {
-        const uint64_t start = A.roff[r], end = A.roff[r + 1];
-        if (end < start || end > A.n_bases) {
+    for (uint64_t r = (uint64_t)blockIdx.x * SEED_WARPS + warp; r < io.n_reads; r += total_warps) {
+        const uint64_t start = io.roff[r], end = io.roff[r + 1];
+        if (end < start || end > io.n_bases) {
             if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_OFFSETS); A.qcnt[r] = 0; }
             continue;
         }
         const uint64_t n64 = end - start;
-        if (n64 > MT_MAX_READ_LEN) {
+        if (n64 > io.max_len) {
             if (lane == 0) { atomicOr(&A.ctr->err, ERR_READ_TOO_LONG); A.qcnt[r] = 0; }
             continue;
         }
         const uint32_t n = (uint32_t)n64;
-        if (warp_pack(A.reads, A.n_bases, A.vec_ok, start, n, ws.rd)) {
+        if (warp_pack(io.reads, io.n_bases, io.vec_ok, start, n, ws.rd)) {
             if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_BASE); A.qcnt[r] = 0; }
             continue;
         }
         {   // packed read for the approximation stage
-            uint64_t *dst = A.rw + seq_word(start, A.off0, r);
+            uint64_t *dst = A.rw + seq_word(start, io.off0, r);
             for (uint32_t t = lane; t < (n + 31) / 32; t += 32) dst[t] = ws.rd[t];
         }
         const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
@@ -553,10 +549,11 @@ __global__ void k_mask(const unsigned long long *hits, uint32_t G, uint32_t num,
 }
 
 // ---- candidate selection ----------------------------------------------------------------------
-__global__ void k_select(uint64_t n_reads, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep,
+__global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep,
                          uint32_t top_n, Cluster *cand, uint8_t *nloc_ws, uint32_t *cl, uint32_t *fb_list,
                          Counters *ctr) {
     const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t n_reads = io->n_reads;
     for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t r = r0 + threadIdx.x;
         uint32_t taken = 0;
@@ -593,8 +590,8 @@ __global__ void k_select(uint64_t n_reads, const uint32_t *qcnt, const Cluster *
 // ---- exact slow path -------------------------------------------------------------------------------
 struct FbArgs {
     IndexView ix;
-    const uint64_t *rw, *roff;
-    uint64_t off0;
+    const uint64_t *rw;
+    const IoBlock *io;
     uint32_t e_abs, e_permille, min_seeds, max_occ, top_n;
     const uint8_t *keep;
     const uint32_t *fb_list;
@@ -634,10 +631,10 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(FbArgs A) {
     const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
     for (uint64_t fi = blockIdx.x; fi < A.ctr->fb_count; fi += gridDim.x) {
         const uint32_t r = A.fb_list[fi];
-        const uint64_t start = A.roff[r];
-        const uint32_t n = (uint32_t)(A.roff[r + 1] - start);
+        const uint64_t start = A.io->roff[r];
+        const uint32_t n = (uint32_t)(A.io->roff[r + 1] - start);
         const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
-        const uint64_t *rd = A.rw + seq_word(start, A.off0, r);
+        const uint64_t *rd = A.rw + seq_word(start, A.io->off0, r);
         if (threadIdx.x == 0) s_H = 0;
         __syncthreads();
         const uint32_t nwin = n - k - w + 2;   // the read reached here, so it has windows
@@ -732,15 +729,11 @@ __global__ void __launch_bounds__(FB_THREADS) k_fallback(FbArgs A) {
 
 // ---- per-read decision -------------------------------------------------------------------------------
 struct DecideArgs {
-    uint64_t n_reads;
-    const uint64_t *roff;
+    const IoBlock *io;
     uint32_t e_abs, e_permille, top_n;
     const uint8_t *nloc_ws;
     const Cluster *cand;
     const uint8_t *dist;
-    int32_t *taxon;
-    uint8_t *nloc;
-    mt_loc *locs;
     unsigned long long *U;
     int32_t *multi_set;
     uint32_t *multi_list;
@@ -750,12 +743,13 @@ struct DecideArgs {
 __global__ void k_decide(DecideArgs A) {
     const uint32_t lane = threadIdx.x & 31u;
     unsigned long long acc = 0, mul = 0, cand = 0;
-    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < A.n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
+    const IoBlock io = *A.io;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < io.n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t r = r0 + threadIdx.x;
         int32_t uniq = -1;
         bool is_multi = false;
-        if (r < A.n_reads) {
-            uint32_t n = (uint32_t)(A.roff[r + 1] - A.roff[r]);
+        if (r < io.n_reads) {
+            uint32_t n = (uint32_t)(io.roff[r + 1] - io.roff[r]);
             uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
             uint32_t nl = A.nloc_ws[r];
             cand += nl;
@@ -787,10 +781,10 @@ __global__ void k_decide(DecideArgs A) {
                         if (!seen) S[ns++] = g;
                     }
                 }
-                if (A.locs) A.locs[r * A.top_n + t] = L;
+                if (io.locs) io.locs[r * A.top_n + t] = L;
             }
-            A.taxon[r] = tax;
-            if (A.nloc) A.nloc[r] = (uint8_t)nl;
+            io.taxon[r] = tax;
+            if (io.nloc) io.nloc[r] = (uint8_t)nl;
             if (ns == 1) uniq = S[0];
             if (ns >= 2) {
                 is_multi = true;
@@ -895,7 +889,7 @@ namespace {
 
 struct Layout {
     size_t rw, qcnt, clus, keep, ghits, cand, nloc_ws, cl, dist, fb_list, multi_list, multi_set, U, M, abund,
-        ctr, fb_scratch, taxon, nloc, locs, reads, roff, total;
+        ctr, io, fb_scratch, taxon, nloc, locs, reads, roff, total;
     uint64_t rw_words, fb_cap;
 };
 
@@ -928,6 +922,7 @@ Layout plan_layout(const mt_index *ix, uint64_t n_bases, uint64_t n_reads, uint3
     L.M = c.take<double>(ix->G);
     L.abund = c.take<double>(ix->G);
     L.ctr = c.take<Counters>(1);
+    L.io = c.take<IoBlock>(1);
     L.fb_cap = fb_cap_for(maxn, ix->k, ix->w, max_occ);
     L.fb_scratch = c.take<uint8_t>((uint64_t)FB_CTAS * L.fb_cap * 12);
     if (host_io) {
@@ -956,6 +951,160 @@ int check_params(const mt_classify_params *p) {
 
 }  // namespace
 
+namespace mt {
+
+// Everything one classification enqueues once its inputs are on the device and its IoBlock
+// is written: no allocation, no synchronisation and no host read, so it can be captured into
+// a CUDA graph. Grids are sized for the capacity `cap_reads`; the kernels take the actual
+// batch size from the IoBlock and later counts from device counters.
+struct EnqueueCtx {
+    const mt_index *ix;
+    const mt_classify_params *p;
+    const Layout *L;
+    unsigned char *ws;
+    uint64_t cap_reads;
+    uint32_t maxn, maxE;
+    bool allow_tune;
+    cudaEvent_t *ev;       // 5 events or null
+    uint64_t launches;
+};
+
+static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
+    const Layout &L = *c.L;
+    const mt_classify_params *p = c.p;
+    const mt_index *ix = c.ix;
+    const uint32_t G = ix->G, top_n = p->top_n;
+    auto P = [&](size_t off) { return (void *)(c.ws + off); };
+    auto mark = [&](int i) { if (c.ev) cudaEventRecord(c.ev[i], s); };
+    Counters *ctr = (Counters *)P(L.ctr);
+    unsigned long long *ghits = (unsigned long long *)P(L.ghits);
+    unsigned long long *U = (unsigned long long *)P(L.U);
+    double *M = (double *)P(L.M);
+    const IoBlock *io = (const IoBlock *)P(L.io);
+    MT_CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+    MT_CK(cudaMemsetAsync(ghits, 0, G * 8, s));
+    MT_CK(cudaMemsetAsync(U, 0, G * 8, s));
+    MT_CK(cudaMemsetAsync(M, 0, G * 8, s));
+    const IndexView iv = ix->view();
+    mark(0);
+    if (c.cap_reads) {
+        SeedArgs A;
+        A.ix = iv;
+        A.io = io;
+        A.e_abs = p->e_abs; A.e_permille = p->e_permille; A.min_seeds = p->min_seeds; A.max_occ = p->max_occ;
+        A.rw = (uint64_t *)P(L.rw);
+        A.qcnt = (uint32_t *)P(L.qcnt);
+        A.clus = (Cluster *)P(L.clus);
+        A.ghits = ghits;
+        A.fb_list = (uint32_t *)P(L.fb_list);
+        A.ctr = ctr;
+        const bool smem_hist = G <= SMEM_HIST_MAX;
+        const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem);
+        int per_sm = 0;
+        if (smem_hist) {
+            MT_CK(cudaFuncSetAttribute(k_seed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<true>, SEED_THREADS, smem));
+        } else {
+            MT_CK(cudaFuncSetAttribute(k_seed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<false>, SEED_THREADS, smem));
+        }
+        per_sm = std::max(per_sm, 1);
+        const uint64_t need = (c.cap_reads + SEED_WARPS - 1) / SEED_WARPS;
+        const unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
+        if (smem_hist) k_seed<true><<<grid, SEED_THREADS, smem, s>>>(A);
+        else k_seed<false><<<grid, SEED_THREADS, smem, s>>>(A);
+        MT_CK(cudaGetLastError());
+        mark(1);
+
+        k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
+        MT_CK(cudaGetLastError());
+        const unsigned rblocks = (unsigned)std::min<uint64_t>((c.cap_reads + 255) / 256, (uint64_t)sm_count() * 8);
+        k_select<<<rblocks, 256, 0, s>>>(io, A.qcnt, A.clus, (const uint8_t *)P(L.keep), top_n, (Cluster *)P(L.cand),
+                                         (uint8_t *)P(L.nloc_ws), (uint32_t *)P(L.cl), A.fb_list, ctr);
+        MT_CK(cudaGetLastError());
+        FbArgs F;
+        F.ix = iv;
+        F.rw = A.rw;
+        F.io = io;
+        F.e_abs = p->e_abs; F.e_permille = p->e_permille; F.min_seeds = p->min_seeds; F.max_occ = p->max_occ;
+        F.top_n = top_n;
+        F.keep = (const uint8_t *)P(L.keep);
+        F.fb_list = A.fb_list;
+        F.cand = (Cluster *)P(L.cand);
+        F.nloc_ws = (uint8_t *)P(L.nloc_ws);
+        F.cl = (uint32_t *)P(L.cl);
+        F.ctr = ctr;
+        F.scratch = (uint64_t *)P(L.fb_scratch);
+        F.cap = L.fb_cap;
+        k_fallback<<<FB_CTAS, FB_THREADS, 0, s>>>(F);
+        MT_CK(cudaGetLastError());
+        mark(2);
+
+        int rc = launch_classify_eda(iv, A.rw, io, (const uint32_t *)P(L.cl), &ctr->cl_count, c.cap_reads * top_n,
+                                     (const Cluster *)P(L.cand), top_n, p->e_abs, p->e_permille, c.maxn, c.maxE,
+                                     p->eda_mode, (uint8_t *)P(L.dist), &ctr->eda_counter, s, c.allow_tune);
+        if (rc) return rc;
+        mark(3);
+
+        DecideArgs D;
+        D.io = io;
+        D.e_abs = p->e_abs; D.e_permille = p->e_permille; D.top_n = top_n;
+        D.nloc_ws = (const uint8_t *)P(L.nloc_ws);
+        D.cand = (const Cluster *)P(L.cand);
+        D.dist = (const uint8_t *)P(L.dist);
+        D.U = U;
+        D.multi_set = (int32_t *)P(L.multi_set);
+        D.multi_list = (uint32_t *)P(L.multi_list);
+        D.ctr = ctr;
+        k_decide<<<rblocks, 256, 0, s>>>(D);
+        MT_CK(cudaGetLastError());
+        k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(D.multi_list, ctr, D.multi_set, top_n, U, M);
+        MT_CK(cudaGetLastError());
+        c.launches += 7;   // seed, mask, select, fallback, approximation, decide, multi
+    } else {
+        mark(1); mark(2); mark(3);
+    }
+    k_abund<<<1, 1024, 0, s>>>(G, U, M, p->abund_cutoff, (double *)P(L.abund));
+    MT_CK(cudaGetLastError());
+    c.launches += 1;
+    mark(4);
+    return MT_OK;
+}
+
+static void fill_stats(mt_stats *st, const Counters &h, uint64_t n_reads, uint64_t ws_bytes, uint64_t launches,
+                       cudaEvent_t *ev) {
+    if (!st) return;
+    st->n_reads = n_reads;
+    st->n_minimizers = h.stat[ST_MINS];
+    st->n_hits = h.stat[ST_HITS];
+    st->n_candidates = h.stat[ST_CAND];
+    st->n_accepted = h.stat[ST_ACC];
+    st->n_multi = h.stat[ST_MULTI];
+    st->n_fallback = h.stat[ST_FB];
+    st->workspace_bytes = ws_bytes;
+    st->n_ext_occ = h.stat[ST_EXT];
+    st->n_stored = h.stat[ST_STORED];
+    st->n_launches = launches;
+    st->err_bits = h.err;
+    st->ms_seed = st->ms_select = st->ms_eda = st->ms_profile = st->ms_total = 0;
+    if (ev) {
+        float t[4] = {0, 0, 0, 0}, tot = 0;
+        for (int i = 0; i < 4; i++) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
+        cudaEventElapsedTime(&tot, ev[0], ev[4]);
+        st->ms_seed = t[0]; st->ms_select = t[1]; st->ms_eda = t[2]; st->ms_profile = t[3]; st->ms_total = tot;
+    }
+}
+
+static int status_of(uint32_t err) {
+    if (err & (ERR_BAD_BASE | ERR_BAD_OFFSETS | ERR_READ_TOO_LONG)) return MT_EINVAL;
+    if (err) return MT_ECUDA;
+    return MT_OK;
+}
+
+}  // namespace mt
+
+using namespace mt;
+
 uint64_t mt::classify_ws_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
                                const mt_classify_params *p, uint32_t maxn, bool host_io) {
     if (!ix || !p || check_params(p)) return 0;
@@ -973,7 +1122,7 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
                            uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
                            int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
                            mt_stats *stats) {
-    if (!ix || !offsets || !taxon || (!reads && n_bases)) return MT_EINVAL;
+    if (!ix || !offsets || (!taxon && n_reads) || (!reads && n_bases)) return MT_EINVAL;
     int rc = check_params(p);
     if (rc) return rc;
     if (n_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
@@ -984,8 +1133,7 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
 
     // longest read and offset checks
     uint32_t maxn = 0;
-    uint64_t off0 = 0;
-    Counters *pre = nullptr;
+    uint64_t off0 = 0, launches = 0;
     if (host_io) {
         if (n_reads) off0 = offsets[0];
         for (uint64_t r = 0; r < n_reads; r++) {
@@ -993,11 +1141,13 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
             maxn = (uint32_t)std::max<uint64_t>(maxn, std::min<uint64_t>(offsets[r + 1] - offsets[r], 0xFFFFFFFFull));
         }
     } else if (n_reads) {
+        Counters *pre = nullptr;
         if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) return rc;
         MT_CK(cudaMemsetAsync(pre, 0, sizeof(Counters), s));
         unsigned blocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 4);
         k_maxlen<<<blocks, 256, 0, s>>>(offsets, n_reads, n_bases, pre);
         MT_CK(cudaGetLastError());
+        launches++;
         Counters h{};
         MT_CK(cudaMemcpyAsync(&h, pre, sizeof(h), cudaMemcpyDeviceToHost, s));
         MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
@@ -1014,167 +1164,205 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
     unsigned char *ws = nullptr;
     if ((rc = dalloc((void **)&ws, L.total, s))) return rc;
     auto P = [&](size_t off) { return (void *)(ws + off); };
-    const uint8_t *d_reads = reads;
-    const uint64_t *d_roff = offsets;
-    int32_t *d_taxon = taxon;
-    uint8_t *d_nloc = nloc;
-    mt_loc *d_locs = locs;
+    IoBlock hio;
+    hio.reads = reads;
+    hio.roff = offsets;
+    hio.n_reads = n_reads;
+    hio.n_bases = n_bases;
+    hio.off0 = off0;
+    hio.max_len = MT_MAX_READ_LEN;
+    hio.taxon = taxon;
+    hio.nloc = nloc;
+    hio.locs = locs;
     if (host_io) {
-        d_reads = (const uint8_t *)P(L.reads);
-        d_roff = (const uint64_t *)P(L.roff);
-        d_taxon = (int32_t *)P(L.taxon);
-        d_nloc = (uint8_t *)P(L.nloc);
-        d_locs = locs ? (mt_loc *)P(L.locs) : nullptr;
-        if (n_bases) MT_CK(cudaMemcpyAsync((void *)d_reads, reads, n_bases, cudaMemcpyHostToDevice, s));
-        MT_CK(cudaMemcpyAsync((void *)d_roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+        hio.reads = (const uint8_t *)P(L.reads);
+        hio.roff = (const uint64_t *)P(L.roff);
+        hio.taxon = (int32_t *)P(L.taxon);
+        hio.nloc = (uint8_t *)P(L.nloc);
+        hio.locs = locs ? (mt_loc *)P(L.locs) : nullptr;
+        if (n_bases) MT_CK(cudaMemcpyAsync((void *)hio.reads, reads, n_bases, cudaMemcpyHostToDevice, s));
+        MT_CK(cudaMemcpyAsync((void *)hio.roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
     }
-    Counters *ctr = (Counters *)P(L.ctr);
-    unsigned long long *ghits = (unsigned long long *)P(L.ghits);
-    unsigned long long *U = (unsigned long long *)P(L.U);
-    double *M = (double *)P(L.M);
-    MT_CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
-    MT_CK(cudaMemsetAsync(ghits, 0, G * 8, s));
-    MT_CK(cudaMemsetAsync(U, 0, G * 8, s));
-    MT_CK(cudaMemsetAsync(M, 0, G * 8, s));
+    hio.vec_ok = ((uintptr_t)hio.reads & 15u) == 0;
+    MT_CK(cudaMemcpyAsync(P(L.io), &hio, sizeof(hio), cudaMemcpyHostToDevice, s));
 
-    IndexView iv = ix->view();
-    // stage timing on the call's stream (only when counters are requested)
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    const bool timing = stats != nullptr;
-    if (timing)
+    if (stats)
         for (auto &e : ev) MT_CK(cudaEventCreate(&e));
-    auto mark = [&](int i) { if (timing) cudaEventRecord(ev[i], s); };
-    uint64_t launches = host_io ? 0 : (n_reads ? 1 : 0);   // k_maxlen
-    mark(0);
-    if (n_reads) {
-        SeedArgs A;
-        A.ix = iv;
-        A.reads = d_reads;
-        A.n_bases = n_bases;
-        A.roff = d_roff;
-        A.n_reads = n_reads;
-        A.off0 = off0;
-        A.vec_ok = ((uintptr_t)d_reads & 15u) == 0;
-        A.e_abs = p->e_abs; A.e_permille = p->e_permille; A.min_seeds = p->min_seeds; A.max_occ = p->max_occ;
-        A.rw = (uint64_t *)P(L.rw);
-        A.qcnt = (uint32_t *)P(L.qcnt);
-        A.clus = (Cluster *)P(L.clus);
-        A.ghits = ghits;
-        A.fb_list = (uint32_t *)P(L.fb_list);
-        A.ctr = ctr;
-        bool smem_hist = G <= SMEM_HIST_MAX;
-        size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem);
-        int per_sm = 0;
-        if (smem_hist) {
-            MT_CK(cudaFuncSetAttribute(k_seed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<true>, SEED_THREADS, smem));
-        } else {
-            MT_CK(cudaFuncSetAttribute(k_seed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<false>, SEED_THREADS, smem));
-        }
-        per_sm = std::max(per_sm, 1);
-        uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
-        unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
-        if (smem_hist) k_seed<true><<<grid, SEED_THREADS, smem, s>>>(A);
-        else k_seed<false><<<grid, SEED_THREADS, smem, s>>>(A);
-        MT_CK(cudaGetLastError());
-        mark(1);
+    EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, true, stats ? ev : nullptr, launches};
+    rc = enqueue_classify(ctx, s);
+    if (rc) { dfree(ws, s); return rc; }
 
-        k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
-        MT_CK(cudaGetLastError());
-
-        unsigned rblocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 8);
-        k_select<<<rblocks, 256, 0, s>>>(n_reads, A.qcnt, A.clus, (const uint8_t *)P(L.keep), top_n,
-                                         (Cluster *)P(L.cand), (uint8_t *)P(L.nloc_ws), (uint32_t *)P(L.cl),
-                                         A.fb_list, ctr);
-        MT_CK(cudaGetLastError());
-
-        FbArgs F;
-        F.ix = iv;
-        F.rw = A.rw; F.roff = d_roff; F.off0 = off0;
-        F.e_abs = p->e_abs; F.e_permille = p->e_permille; F.min_seeds = p->min_seeds; F.max_occ = p->max_occ;
-        F.top_n = top_n;
-        F.keep = (const uint8_t *)P(L.keep);
-        F.fb_list = A.fb_list;
-        F.cand = (Cluster *)P(L.cand);
-        F.nloc_ws = (uint8_t *)P(L.nloc_ws);
-        F.cl = (uint32_t *)P(L.cl);
-        F.ctr = ctr;
-        F.scratch = (uint64_t *)P(L.fb_scratch);
-        F.cap = L.fb_cap;
-        k_fallback<<<FB_CTAS, FB_THREADS, 0, s>>>(F);
-        MT_CK(cudaGetLastError());
-        mark(2);
-
-        rc = launch_classify_eda(iv, A.rw, d_roff, off0, (const uint32_t *)P(L.cl), &ctr->cl_count,
-                                 n_reads * top_n, (const Cluster *)P(L.cand), top_n, p->e_abs, p->e_permille,
-                                 std::max<uint32_t>(maxn, 1), maxE, p->eda_mode, (uint8_t *)P(L.dist),
-                                 &ctr->eda_counter, s);
-        if (rc) { dfree(ws, s); return rc; }
-        mark(3);
-        launches += 5;   // seed, mask, select, fallback, approximation
-
-        DecideArgs D;
-        D.n_reads = n_reads; D.roff = d_roff;
-        D.e_abs = p->e_abs; D.e_permille = p->e_permille; D.top_n = top_n;
-        D.nloc_ws = (const uint8_t *)P(L.nloc_ws);
-        D.cand = (const Cluster *)P(L.cand);
-        D.dist = (const uint8_t *)P(L.dist);
-        D.taxon = d_taxon; D.nloc = d_nloc; D.locs = d_locs;
-        D.U = U;
-        D.multi_set = (int32_t *)P(L.multi_set);
-        D.multi_list = (uint32_t *)P(L.multi_list);
-        D.ctr = ctr;
-        k_decide<<<rblocks, 256, 0, s>>>(D);
-        MT_CK(cudaGetLastError());
-        k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(D.multi_list, ctr, D.multi_set, top_n, U, M);
-        MT_CK(cudaGetLastError());
-        launches += 2;
-    } else {
-        mark(1); mark(2); mark(3);
-    }
-    double *d_ab = (double *)P(L.abund);
-    k_abund<<<1, 1024, 0, s>>>(G, U, M, p->abund_cutoff, d_ab);
-    MT_CK(cudaGetLastError());
-    launches += 1;
-    mark(4);
-
-    // outputs
     cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-    if (genome_hits) MT_CK(cudaMemcpyAsync(genome_hits, ghits, G * 8, kind, s));
-    if (abundance) MT_CK(cudaMemcpyAsync(abundance, d_ab, G * 8, kind, s));
+    if (genome_hits) MT_CK(cudaMemcpyAsync(genome_hits, P(L.ghits), G * 8, kind, s));
+    if (abundance) MT_CK(cudaMemcpyAsync(abundance, P(L.abund), G * 8, kind, s));
     if (host_io && n_reads) {
-        MT_CK(cudaMemcpyAsync(taxon, d_taxon, n_reads * 4, cudaMemcpyDeviceToHost, s));
-        if (nloc) MT_CK(cudaMemcpyAsync(nloc, d_nloc, n_reads, cudaMemcpyDeviceToHost, s));
-        if (locs) MT_CK(cudaMemcpyAsync(locs, d_locs, n_reads * top_n * sizeof(mt_loc), cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaMemcpyAsync(taxon, hio.taxon, n_reads * 4, cudaMemcpyDeviceToHost, s));
+        if (nloc) MT_CK(cudaMemcpyAsync(nloc, hio.nloc, n_reads, cudaMemcpyDeviceToHost, s));
+        if (locs) MT_CK(cudaMemcpyAsync(locs, hio.locs, n_reads * top_n * sizeof(mt_loc), cudaMemcpyDeviceToHost, s));
     }
     Counters h{};
-    MT_CK(cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaMemcpyAsync(&h, P(L.ctr), sizeof(h), cudaMemcpyDeviceToHost, s));
     dfree(ws, s);
     MT_CK(cudaStreamSynchronize(s));
-    if (stats) {
-        stats->n_reads = n_reads;
-        stats->n_minimizers = h.stat[ST_MINS];
-        stats->n_hits = h.stat[ST_HITS];
-        stats->n_candidates = h.stat[ST_CAND];
-        stats->n_accepted = h.stat[ST_ACC];
-        stats->n_multi = h.stat[ST_MULTI];
-        stats->n_fallback = h.stat[ST_FB];
-        stats->workspace_bytes = L.total;
-        stats->n_ext_occ = h.stat[ST_EXT];
-        stats->n_stored = h.stat[ST_STORED];
-        stats->n_launches = launches;
-        float t[4] = {0, 0, 0, 0}, tot = 0;
-        for (int i = 0; i < 4; i++) cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]);
-        cudaEventElapsedTime(&tot, ev[0], ev[4]);
-        stats->ms_seed = t[0];
-        stats->ms_select = t[1];
-        stats->ms_eda = t[2];
-        stats->ms_profile = t[3];
-        stats->ms_total = tot;
+    fill_stats(stats, h, n_reads, L.total, ctx.launches, stats ? ev : nullptr);
+    if (stats)
         for (auto &e : ev) cudaEventDestroy(e);
+    return status_of(h.err);
+}
+
+// ---- plans: preallocated workspace + captured CUDA graph ---------------------------------------------
+struct mt_plan {
+    const mt_index *ix = nullptr;
+    mt_classify_params p{};
+    uint64_t cap_reads = 0, cap_bases = 0;
+    uint32_t max_len = 0, maxE = 0;
+    Layout L{};
+    unsigned char *ws = nullptr;
+    IoBlock *h_io = nullptr;        // pinned
+    Counters *h_ctr = nullptr;      // pinned
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
+    uint64_t calls = 0, launches = 0;
+};
+
+extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, uint64_t max_reads,
+                              uint64_t max_bases, uint32_t max_read_len, mt_plan **out) {
+    if (!out) return MT_EINVAL;
+    *out = nullptr;
+    if (!ix || check_params(p) || max_reads == 0 || max_read_len == 0 || max_read_len > MT_MAX_READ_LEN)
+        return MT_EINVAL;
+    if (max_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
+    const uint32_t maxE = edit_threshold(max_read_len, p->e_abs, p->e_permille);
+    if (maxE > MT_MAX_E) return MT_EINVAL;
+    mt_plan *pl = new mt_plan();
+    pl->ix = ix;
+    pl->p = *p;
+    pl->cap_reads = max_reads;
+    pl->cap_bases = max_bases;
+    pl->max_len = max_read_len;
+    pl->maxE = maxE;
+    pl->L = plan_layout(ix, max_bases, max_reads, p->top_n, max_read_len, p->max_occ, true);
+    cudaError_t e = cudaMalloc((void **)&pl->ws, pl->L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return e == cudaErrorMemoryAllocation ? MT_ENOMEM : MT_ECUDA;
     }
-    if (h.err & (ERR_BAD_BASE | ERR_BAD_OFFSETS | ERR_READ_TOO_LONG)) return MT_EINVAL;
-    if (h.err) return MT_ECUDA;
+    if (cudaMallocHost((void **)&pl->h_io, sizeof(IoBlock)) != cudaSuccess ||
+        cudaMallocHost((void **)&pl->h_ctr, sizeof(Counters)) != cudaSuccess) {
+        cudaFree(pl->ws);
+        cudaFreeHost(pl->h_io);
+        delete pl;
+        return MT_ENOMEM;
+    }
+    *out = pl;
     return MT_OK;
+}
+
+extern "C" uint64_t mt_plan_device_bytes(const mt_plan *pl) { return pl ? pl->L.total : 0; }
+
+extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                                uint64_t n_reads, int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc,
+                                mt_loc *locs, uint64_t *genome_hits, double *abundance, mt_stats *stats) {
+    if (!pl || !offsets || (!taxon && n_reads) || (!reads && n_bases)) return MT_EINVAL;
+    if (n_reads > pl->cap_reads || n_bases > pl->cap_bases) return MT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Layout &L = pl->L;
+    const uint32_t G = pl->ix->G, top_n = pl->p.top_n;
+    const bool host_io = !device_ptrs;
+    auto P = [&](size_t off) { return (void *)(pl->ws + off); };
+    if (stats) memset(stats, 0, sizeof(*stats));
+    uint64_t off0 = 0;
+    if (host_io) {
+        if (n_reads) off0 = offsets[0];
+        for (uint64_t r = 0; r < n_reads; r++) {
+            if (offsets[r + 1] < offsets[r] || offsets[r + 1] > n_bases) return MT_EINVAL;
+            if (offsets[r + 1] - offsets[r] > pl->max_len) return MT_EINVAL;
+        }
+    } else if (n_reads) {
+        MT_CK(cudaMemcpyAsync(&pl->h_ctr->stat[0], offsets, 8, cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaStreamSynchronize(s));
+        off0 = pl->h_ctr->stat[0];
+    }
+    IoBlock &io = *pl->h_io;
+    io.reads = reads; io.roff = offsets; io.n_reads = n_reads; io.n_bases = n_bases; io.off0 = off0;
+    io.max_len = pl->max_len;
+    io.taxon = taxon; io.nloc = nloc; io.locs = locs;
+    if (host_io) {
+        io.reads = (const uint8_t *)P(L.reads);
+        io.roff = (const uint64_t *)P(L.roff);
+        io.taxon = (int32_t *)P(L.taxon);
+        io.nloc = (uint8_t *)P(L.nloc);
+        io.locs = locs ? (mt_loc *)P(L.locs) : nullptr;
+        if (n_bases) MT_CK(cudaMemcpyAsync((void *)io.reads, reads, n_bases, cudaMemcpyHostToDevice, s));
+        MT_CK(cudaMemcpyAsync((void *)io.roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+    }
+    io.vec_ok = ((uintptr_t)io.reads & 15u) == 0;
+    MT_CK(cudaMemcpyAsync(P(L.io), pl->h_io, sizeof(IoBlock), cudaMemcpyHostToDevice, s));
+
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (stats) {
+        MT_CK(cudaEventCreate(&ev[0]));
+        MT_CK(cudaEventCreate(&ev[1]));
+        MT_CK(cudaEventRecord(ev[0], s));
+    }
+    EnqueueCtx ctx{pl->ix, &pl->p, &L, pl->ws, pl->cap_reads, pl->max_len, pl->maxE, true, nullptr, 0};
+    int rc = MT_OK;
+    if (pl->calls == 0) {
+        // the first call runs directly (it may autotune the approximation kernel)
+        rc = enqueue_classify(ctx, s);
+        pl->launches = ctx.launches;
+    } else {
+        if (!pl->exec) {
+            // capture on the plan's own stream (the caller's may be the legacy default
+            // stream, which cannot be captured); the graph is then launched on the caller's
+            ctx.allow_tune = false;
+            if (!pl->cap_stream) MT_CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+            MT_CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_classify(ctx, pl->cap_stream);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(pl->cap_stream, &g);
+            if (rc == MT_OK && !cuda_ok(e, "cudaStreamEndCapture")) rc = MT_ECUDA;
+            if (rc == MT_OK && !cuda_ok(cudaGraphInstantiate(&pl->exec, g, 0), "cudaGraphInstantiate")) rc = MT_ECUDA;
+            pl->graph = g;
+            pl->launches = ctx.launches;
+        }
+        if (rc == MT_OK) MT_CK(cudaGraphLaunch(pl->exec, s));
+    }
+    if (rc) return rc;
+    if (stats) MT_CK(cudaEventRecord(ev[1], s));
+    cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (genome_hits) MT_CK(cudaMemcpyAsync(genome_hits, P(L.ghits), G * 8, kind, s));
+    if (abundance) MT_CK(cudaMemcpyAsync(abundance, P(L.abund), G * 8, kind, s));
+    if (host_io && n_reads) {
+        MT_CK(cudaMemcpyAsync(taxon, io.taxon, n_reads * 4, cudaMemcpyDeviceToHost, s));
+        if (nloc) MT_CK(cudaMemcpyAsync(nloc, io.nloc, n_reads, cudaMemcpyDeviceToHost, s));
+        if (locs) MT_CK(cudaMemcpyAsync(locs, io.locs, n_reads * top_n * sizeof(mt_loc), cudaMemcpyDeviceToHost, s));
+    }
+    MT_CK(cudaMemcpyAsync(pl->h_ctr, P(L.ctr), sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    pl->calls++;
+    const Counters h = *pl->h_ctr;
+    fill_stats(stats, h, n_reads, L.total, pl->launches, nullptr);
+    if (stats) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        stats->ms_total = ms;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    return status_of(h.err);
+}
+
+extern "C" void mt_plan_destroy(mt_plan *pl) {
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    cudaFree(pl->ws);
+    cudaFreeHost(pl->h_io);
+    cudaFreeHost(pl->h_ctr);
+    delete pl;
 }

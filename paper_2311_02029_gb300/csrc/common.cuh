@@ -156,6 +156,18 @@ __host__ __device__ __forceinline__ uint32_t edit_threshold(uint32_t n, uint32_t
     return e_permille ? (uint32_t)(((uint64_t)n * e_permille) / 1000u) : e_abs;
 }
 
+// Per-call inputs and outputs of a classification, read by the kernels from device memory so
+// that one captured CUDA graph serves every batch up to its capacity.
+struct IoBlock {
+    const uint8_t *reads;
+    const uint64_t *roff;
+    uint64_t n_reads, n_bases, off0;
+    uint32_t vec_ok, max_len;
+    int32_t *taxon;
+    uint8_t *nloc;
+    mt_loc *locs;
+};
+
 // Location record kept between the seeding and selection passes (16 bytes).
 struct Cluster {
     uint64_t hkey;     // hit key of its first match (genome, rel, first diagonal)

@@ -69,8 +69,8 @@ MT_DEV uint64_t genome_get32(const uint64_t *g, uint64_t nwg, int64_t pos) {
 // obstacles.
 struct ClassifySrc {
     IndexView ix;
-    const uint64_t *rw, *roff;
-    uint64_t off0;
+    const uint64_t *rw;
+    const IoBlock *io;
     const uint32_t *cl;      // compact candidate slots
     const Cluster *cand;     // per slot (read * top_n + t)
     uint32_t top_n, e_abs, e_permille;
@@ -81,10 +81,11 @@ struct ClassifySrc {
         uint32_t s = cl[i];
         uint32_t r = s / top_n;
         Cluster c = cand[s];
+        const uint64_t *roff = io->roff;
         uint64_t ro = roff[r];
         uint32_t n = (uint32_t)(roff[r + 1] - ro);
         uint32_t E = edit_threshold(n, e_abs, e_permille);
-        const uint64_t *rs = rw + seq_word(ro, off0, r);
+        const uint64_t *rs = rw + seq_word(ro, io->off0, r);
         uint32_t nr = (n + 31) / 32;
         if (hk_rel(c.hkey)) {
             for (uint32_t t = gl; t < nr + 2; t += G) {
@@ -388,13 +389,13 @@ static int autotune_class(const Src &src, const uint32_t *perm, uint64_t b, uint
 }
 
 // ---- classification EDA (called by mt_classify) ------------------------------------------------
-int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const uint64_t *roff, uint64_t off0,
+int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *io,
                         const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
                         const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
                         uint32_t maxn, uint32_t maxE, uint32_t mode, uint8_t *dist,
-                        unsigned long long *counter, cudaStream_t s) {
+                        unsigned long long *counter, cudaStream_t s, bool allow_tune) {
     ClassifySrc src;
-    src.ix = ix; src.rw = rw; src.roff = roff; src.off0 = off0; src.cl = cl; src.cand = cand;
+    src.ix = ix; src.rw = rw; src.io = io; src.cl = cl; src.cand = cand;
     src.top_n = top_n; src.e_abs = e_abs; src.e_permille = e_permille; src.dist = dist;
     uint32_t rww = eda_read_words(maxn), www = eda_win_words(maxn, maxE);
     if (mode == MT_EDA_PLAIN)
@@ -403,7 +404,8 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const uint64_t 
     cudaGetDevice(&dev);
     const uint32_t slot = MAX_CLASSES + e_class(maxE);
     uint32_t G = 0;
-    if (!tuned_G(dev, slot, &G)) {
+    if (!tuned_G(dev, slot, &G) && !allow_tune) G = default_G(maxE);
+    if (!G) {
         // time every lanes-per-pair choice on the first 2^17 candidates of this call
         cudaEvent_t e0, e1;
         MT_CK(cudaEventCreate(&e0));

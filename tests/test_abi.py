@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(mtlib):
     assert ctypes.sizeof(mtlib.IndexParams) == 16
     assert ctypes.sizeof(mtlib.ClassifyParams) == 40
     assert mtlib.LOC_DTYPE.itemsize == 24
-    assert ctypes.sizeof(mtlib.Stats) == 128
+    assert ctypes.sizeof(mtlib.Stats) == 136
     assert ctypes.sizeof(mtlib.IndexInfo) == 56
 
 

@@ -199,6 +199,31 @@ def test_masked_genomes_exhaust_stored_locations(mt):
     assert out["stats"]["n_fallback"] >= 15
 
 
+def test_plan_graph_replays_match_oracle(mt, clade):
+    """A plan captured into a CUDA graph on its second call serves batches of different sizes
+    (host and device buffers) with results identical to mt_classify and the oracle."""
+    import torch
+    c, g, r, ix, oix = clade
+    prm = _params(c)
+    plan = mt.Plan(ix, max_reads=8000, max_bases=8000 * 150, max_read_len=150, **prm)
+    cuts = [(0, 5000), (5000, 5300), (7000, 15000), (100, 7100), (15000, 15001), (300, 300)]
+    for i, (a, b) in enumerate(cuts):
+        seq = r.seq[int(r.offsets[a]):int(r.offsets[b])]
+        off = (r.offsets[a:b + 1] - r.offsets[a]).astype(np.uint64)
+        ref = oracle.classify(oix, seq, off, oracle_params(prm), threads=8)
+        if i % 2:
+            out = plan.classify(torch.from_numpy(seq.copy()).cuda(), torch.from_numpy(off.astype(np.int64)).cuda())
+        else:
+            out = plan.classify(seq, off)
+        compare_classify(out, ref)
+        direct = mt.classify(ix, seq, off, **prm)
+        assert np.array_equal(np.asarray(out["taxon"].cpu() if hasattr(out["taxon"], "cpu") else out["taxon"]),
+                              direct["taxon"])
+    with pytest.raises(mt.MtError):
+        plan.classify(r.seq, r.offsets)            # above the capacity
+    plan.close()
+
+
 def test_invalid_inputs(mt, tiny):
     c, g, r, ix, oix = tiny
     prm = _params(c)
