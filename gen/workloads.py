@@ -198,24 +198,26 @@ def _substitute(rng: np.random.Generator, codes: np.ndarray, rate: float, gc: fl
 def make_genomes(c: dict) -> Genomes:
     """Clade-structured reference: ``n_genomes / clade_size`` clade roots with a per-clade
     GC content, members are substitution-mutated copies of the root (divergence drawn
-    uniformly per member). ``clade_size == 1`` gives independent genomes."""
-    rng = np.random.Generator(np.random.PCG64(c["genome_seed"]))
+    uniformly per member). ``clade_size == 1`` gives independent genomes. Clades are drawn on
+    threads, each from its own child seed, so the result does not depend on the thread count."""
     G, L, cs = c["n_genomes"], c["genome_len"], c["clade_size"]
     n_clades = G // cs
     seq = np.empty(G * L, dtype=np.uint8)
     clade = np.repeat(np.arange(n_clades, dtype=np.int32), cs)
-    g = 0
-    for cl in range(n_clades):
+
+    def one(cl, rng):
         gc = float(rng.uniform(*c["gc"]))
         root = _draw_codes(rng, L, gc)
         for m in range(cs):
+            g = cl * cs + m
             if cs == 1:
                 member = root
             else:
                 div = float(rng.uniform(*c["divergence"]))
                 member = _substitute(rng, root, div, gc)
             seq[g * L:(g + 1) * L] = ASCII[member]
-            g += 1
+
+    _run_chunks(one, n_clades, c["genome_seed"])
     offsets = np.arange(G + 1, dtype=np.uint64) * np.uint64(L)
     return Genomes(seq=seq, offsets=offsets, clade=clade)
 

@@ -185,10 +185,12 @@ int mt_plan_classify(mt_plan *plan, const uint8_t *reads, uint64_t n_bases, cons
 uint64_t mt_plan_device_bytes(const mt_plan *plan);
 void mt_plan_destroy(mt_plan *plan);
 
-/* Device bytes of scratch that one mt_classify call needs for this batch shape
- * (inputs and outputs not included). Used for admission control. */
+/* Device bytes that one mt_classify call with HOST buffers allocates for this batch shape
+ * (workspace plus device staging of the inputs and outputs); max_read_len is the batch's
+ * longest read (0: unknown, the bound min(n_bases, MT_MAX_READ_LEN) is used). The serving loop
+ * charges exactly this figure against its HBM budget. 0 for invalid parameters. */
 uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
-                                     const mt_classify_params *params);
+                                     uint32_t max_read_len, const mt_classify_params *params);
 
 /* ---- 2-bit packing (used by the seeding kernels; exposed for the EDA batch call) ---------
  * seq/offsets/words: DEVICE pointers. Writes sequence i at word (offsets[i] >> 5) + i;

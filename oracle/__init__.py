@@ -41,7 +41,7 @@ def build() -> str:
     with _lock:
         if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
             tmp = _SO + ".%d.tmp" % os.getpid()
-            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC])
+            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
             os.replace(tmp, _SO)
     return _SO
 
@@ -58,6 +58,8 @@ def _L():
         lib.or_minimizers.argtypes = [vp, u64, u32, u32, u32, vp, vp, vp, vp]
         lib.or_build_index.restype = vp
         lib.or_build_index.argtypes = [vp, vp, u32, u32, u32, u32, ctypes.POINTER(ctypes.c_int)]
+        lib.or_build_index_threads.restype = vp
+        lib.or_build_index_threads.argtypes = [vp, vp, u32, u32, u32, u32, u32, ctypes.POINTER(ctypes.c_int)]
         lib.or_free_index.argtypes = [vp]
         lib.or_index_n_occ.restype = u64
         lib.or_index_n_occ.argtypes = [vp]
@@ -119,14 +121,19 @@ def minimizers(seq, k: int, w: int, canonical: int):
 class Index:
     """The oracle's reference index: all genome minimizers sorted by k-mer code."""
 
-    def __init__(self, seq, offsets, k: int, w: int, canonical: int):
+    def __init__(self, seq, offsets, k: int, w: int, canonical: int, threads: int = 1):
+        """``threads > 1`` builds the same index with the work split over host threads."""
         self.seq = _u8(seq)
         self.offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         self.G = len(self.offsets) - 1
         self.k, self.w, self.canonical = k, w, canonical
         err = ctypes.c_int(0)
-        h = _L().or_build_index(_p(self.seq), _p(self.offsets), self.G, k, w, canonical,
-                                ctypes.byref(err))
+        if threads > 1:
+            h = _L().or_build_index_threads(_p(self.seq), _p(self.offsets), self.G, k, w, canonical, threads,
+                                            ctypes.byref(err))
+        else:
+            h = _L().or_build_index(_p(self.seq), _p(self.offsets), self.G, k, w, canonical,
+                                    ctypes.byref(err))
         if not h:
             raise OracleError("or_build_index failed: %d" % err.value)
         self._h = ctypes.c_void_p(h)

@@ -563,3 +563,150 @@ const uint8_t *or_index_codes(const or_index *ix, uint32_t g, uint64_t *len) {
     *len = ix->goff[g + 1] - ix->goff[g];
     return ix->codes + ix->goff[g];
 }
+
+/* ---- the same index built on several host threads (verification runs only) ----------------
+ * Identical contents to or_build_index: every genome's minimizers are found by the same
+ * routine on a pool of threads, then the records are distributed into buckets by the top bits
+ * of their code (bucket order = code order) and each bucket is sorted by (code, genome,
+ * position) on the pool. Only the work is split; nothing is computed differently. */
+#include <pthread.h>
+
+typedef struct {
+    const or_index *ix;
+    uint32_t next_g;          /* shared work counter */
+    pthread_mutex_t mu;
+    uint64_t **pos;           /* per genome */
+    uint64_t **code;
+    uint8_t **strand;
+    int64_t *cnt;
+    int err;
+} mt_job;
+
+static void *mini_worker(void *arg) {
+    mt_job *J = arg;
+    const or_index *ix = J->ix;
+    uint64_t scap = 0;
+    uint64_t *spos = NULL, *scode = NULL;
+    uint8_t *sst = NULL;
+    for (;;) {
+        pthread_mutex_lock(&J->mu);
+        uint32_t g = J->next_g++;
+        pthread_mutex_unlock(&J->mu);
+        if (g >= ix->G) break;
+        uint64_t len = ix->goff[g + 1] - ix->goff[g];
+        uint64_t cap = len ? len : 1;
+        if (cap > scap) {   /* thread scratch, then exact-size copies per genome */
+            free(spos); free(scode); free(sst);
+            spos = malloc(cap * sizeof(uint64_t));
+            scode = malloc(cap * sizeof(uint64_t));
+            sst = malloc(cap);
+            scap = (spos && scode && sst) ? cap : 0;
+        }
+        if (!scap) { J->cnt[g] = OR_ENOMEM; continue; }
+        int64_t m = minimizers_of_codes(ix->codes + ix->goff[g], len, ix->k, ix->w, ix->canonical,
+                                        scode, NULL, spos, sst);
+        J->cnt[g] = m;
+        if (m <= 0) continue;
+        J->pos[g] = malloc((uint64_t)m * sizeof(uint64_t));
+        J->code[g] = malloc((uint64_t)m * sizeof(uint64_t));
+        J->strand[g] = malloc((uint64_t)m);
+        if (!J->pos[g] || !J->code[g] || !J->strand[g]) { J->cnt[g] = OR_ENOMEM; continue; }
+        memcpy(J->pos[g], spos, (uint64_t)m * sizeof(uint64_t));
+        memcpy(J->code[g], scode, (uint64_t)m * sizeof(uint64_t));
+        memcpy(J->strand[g], sst, (uint64_t)m);
+    }
+    free(spos); free(scode); free(sst);
+    return NULL;
+}
+
+typedef struct {
+    or_occ *occ;
+    uint64_t *bstart;         /* NB + 1 */
+    uint32_t nb;
+    uint32_t next_b;
+    pthread_mutex_t mu;
+} sort_job;
+
+static void *sort_worker(void *arg) {
+    sort_job *S = arg;
+    for (;;) {
+        pthread_mutex_lock(&S->mu);
+        uint32_t b = S->next_b++;
+        pthread_mutex_unlock(&S->mu);
+        if (b >= S->nb) break;
+        qsort(S->occ + S->bstart[b], S->bstart[b + 1] - S->bstart[b], sizeof(or_occ), occ_cmp);
+    }
+    return NULL;
+}
+
+or_index *or_build_index_threads(const uint8_t *seq, const uint64_t *off, uint32_t G, uint32_t k,
+                                 uint32_t w, uint32_t canonical, uint32_t nthreads, int *err) {
+    *err = OR_OK;
+    if (k < 1 || k > 31 || w < 1 || G == 0 || nthreads < 1) { *err = OR_EINVAL; return NULL; }
+    if (nthreads > 256) nthreads = 256;
+    or_index *ix = calloc(1, sizeof(or_index));
+    if (!ix) { *err = OR_ENOMEM; return NULL; }
+    ix->k = k; ix->w = w; ix->canonical = canonical; ix->G = G;
+    uint64_t total = off[G] - off[0];
+    ix->codes = malloc(total ? total : 1);
+    ix->goff = malloc((G + 1) * sizeof(uint64_t));
+    if (!ix->codes || !ix->goff) { *err = OR_ENOMEM; or_free_index(ix); return NULL; }
+    for (uint32_t g = 0; g <= G; g++) ix->goff[g] = off[g] - off[0];
+    for (uint32_t g = 0; g < G; g++)
+        if (off[g + 1] < off[g] || off[g + 1] - off[g] >= (1ULL << 32)) { *err = OR_EINVAL; or_free_index(ix); return NULL; }
+    if (to_codes(seq + off[0], total, ix->codes) != OR_OK) { *err = OR_EINVAL; or_free_index(ix); return NULL; }
+
+    mt_job J;
+    memset(&J, 0, sizeof(J));
+    J.ix = ix;
+    pthread_mutex_init(&J.mu, NULL);
+    J.pos = calloc(G, sizeof(uint64_t *));
+    J.code = calloc(G, sizeof(uint64_t *));
+    J.strand = calloc(G, sizeof(uint8_t *));
+    J.cnt = calloc(G, sizeof(int64_t));
+    pthread_t th[256];
+    for (uint32_t t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, mini_worker, &J);
+    for (uint32_t t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&J.mu);
+    uint64_t n_occ = 0;
+    for (uint32_t g = 0; g < G; g++) {
+        if (J.cnt[g] < 0) *err = (int)J.cnt[g];
+        else n_occ += (uint64_t)J.cnt[g];
+    }
+    /* buckets by the top 12 bits of the 2k-bit code */
+    const uint32_t bits = 2 * k, shift = bits > 12 ? bits - 12 : 0, NB = 1u << (bits > 12 ? 12 : bits);
+    uint64_t *bstart = calloc(NB + 1, sizeof(uint64_t));
+    ix->occ = malloc((n_occ ? n_occ : 1) * sizeof(or_occ));
+    if (*err == OR_OK && (!bstart || !ix->occ)) *err = OR_ENOMEM;
+    if (*err == OR_OK) {
+        for (uint32_t g = 0; g < G; g++)
+            for (int64_t i = 0; i < J.cnt[g]; i++) bstart[(J.code[g][i] >> shift) + 1]++;
+        for (uint32_t b = 0; b < NB; b++) bstart[b + 1] += bstart[b];
+        uint64_t *cur = malloc(NB * sizeof(uint64_t));
+        if (!cur) *err = OR_ENOMEM;
+        else {
+            memcpy(cur, bstart, NB * sizeof(uint64_t));
+            for (uint32_t g = 0; g < G; g++)
+                for (int64_t i = 0; i < J.cnt[g]; i++) {
+                    or_occ *o = &ix->occ[cur[J.code[g][i] >> shift]++];
+                    o->code = J.code[g][i];
+                    o->g = g;
+                    o->pos = (uint32_t)J.pos[g][i];
+                    o->strand = J.strand[g][i];
+                }
+            free(cur);
+        }
+    }
+    for (uint32_t g = 0; g < G; g++) { free(J.pos[g]); free(J.code[g]); free(J.strand[g]); }
+    free(J.pos); free(J.code); free(J.strand); free(J.cnt);
+    if (*err != OR_OK) { free(bstart); or_free_index(ix); return NULL; }
+    ix->n_occ = n_occ;
+    sort_job S;
+    S.occ = ix->occ; S.bstart = bstart; S.nb = NB; S.next_b = 0;
+    pthread_mutex_init(&S.mu, NULL);
+    for (uint32_t t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, sort_worker, &S);
+    for (uint32_t t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&S.mu);
+    free(bstart);
+    return ix;
+}

@@ -98,7 +98,7 @@ def lib():
         L.mt_classify.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
                                   vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.mt_classify_workspace_bytes.restype = u64
-        L.mt_classify_workspace_bytes.argtypes = [vp, u64, u64, ctypes.POINTER(ClassifyParams)]
+        L.mt_classify_workspace_bytes.argtypes = [vp, u64, u64, u32, ctypes.POINTER(ClassifyParams)]
         L.mt_pack_seqs.restype = i32
         L.mt_pack_seqs.argtypes = [vp, vp, u64, vp, vp]
         L.mt_eda_batch.restype = i32
@@ -321,9 +321,10 @@ def locs_from_device(t) -> np.ndarray:
     return np.ascontiguousarray(a).view(LOC_DTYPE).reshape(a.shape[0], a.shape[1])
 
 
-def workspace_bytes(ix: Index, n_bases: int, n_reads: int, **params) -> int:
+def workspace_bytes(ix: Index, n_bases: int, n_reads: int, max_read_len: int = 0, **params) -> int:
+    """Device bytes one host-buffer mt_classify call allocates (what the server charges)."""
     p = classify_params(**params)
-    return int(lib().mt_classify_workspace_bytes(ix.handle, n_bases, n_reads, ctypes.byref(p)))
+    return int(lib().mt_classify_workspace_bytes(ix.handle, n_bases, n_reads, max_read_len, ctypes.byref(p)))
 
 
 # ---- packing and the EDA stage alone -----------------------------------------------------------

@@ -1112,10 +1112,11 @@ uint64_t mt::classify_ws_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_
 }
 
 extern "C" uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_reads,
-                                                const mt_classify_params *p) {
+                                                uint32_t max_read_len, const mt_classify_params *p) {
     if (!ix || !p || check_params(p)) return 0;
-    uint32_t maxn = (uint32_t)std::min<uint64_t>(n_bases, MT_MAX_READ_LEN);
-    return plan_layout(ix, n_bases, n_reads, p->top_n, maxn, p->max_occ, false).total;
+    uint32_t maxn = max_read_len ? std::min<uint32_t>(max_read_len, MT_MAX_READ_LEN)
+                                 : (uint32_t)std::min<uint64_t>(n_bases, MT_MAX_READ_LEN);
+    return plan_layout(ix, n_bases, n_reads, p->top_n, std::max<uint32_t>(maxn, 1), p->max_occ, true).total;
 }
 
 extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,

@@ -1,0 +1,105 @@
+"""GPU tests of the continuous-batching request loop (mt_server_*): every request's result is
+the same when it runs alone and when it runs in a mix of overlapping requests, admission by
+the HBM budget, cancellation and bounded polling."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from helpers import compare_classify, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mt():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2311_02029_gb300 import _build
+    _build.build()
+    import paper_2311_02029_gb300 as m
+    oracle.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def work(mt):
+    c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=30_000)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    prm = dict(e_abs=c["e_abs"], e_permille=0, min_seeds=3, top_n=3, max_occ=1024)
+    return c, g, r, ix, prm
+
+
+def _batch(r, a, b):
+    seq = r.seq[int(r.offsets[a]):int(r.offsets[b])].copy()
+    off = (r.offsets[a:b + 1] - r.offsets[a]).astype(np.uint64)
+    return seq, off
+
+
+def _same(out, ref):
+    assert np.array_equal(out["taxon"], ref["taxon"])
+    assert np.array_equal(out["nloc"], ref["nloc"])
+    for f in ("genome", "seeds", "strand", "dist", "wstart"):
+        assert np.array_equal(out["locs"][f], ref["locs"][f])
+    assert np.array_equal(out["genome_hits"], ref["genome_hits"])
+    assert np.abs(out["abundance"] - ref["abundance"]).max() <= 1e-6
+
+
+def test_results_identical_alone_and_in_the_mix(mt, work):
+    import torch
+    c, g, r, ix, prm = work
+    rng = np.random.default_rng(3)
+    cuts = []
+    for size in (1, 7, 250, 3000, 9000, 120, 5000, 1, 20000, 64, 800, 0):
+        a = int(rng.integers(0, r.n - size + 1))
+        cuts.append((a, a + size))
+    batches = [_batch(r, a, b) for a, b in cuts]
+    alone = [mt.classify(ix, s, o, **prm) for s, o in batches]
+    free, _ = torch.cuda.mem_get_info()
+    srv = mt.Server(ix, hbm_budget=free // 3, max_slots=3, **prm)
+    ids = [srv.submit(s, o) for s, o in batches]          # all in flight together
+    for rid, ref in zip(ids, alone):
+        rc, lat, out = srv.poll(rid, 120_000)
+        assert rc == mt.MT_OK and lat is not None and lat >= 0
+        _same(out, ref)
+    srv.close()
+    # and against the oracle for two of them
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    for (s, o), out in ((batches[4], alone[4]), (batches[8], alone[8])):
+        compare_classify(out, oracle.classify(oix, s, o, oracle_params(prm), threads=8))
+
+
+def test_admission_by_budget(mt, work):
+    c, g, r, ix, prm = work
+    small = _batch(r, 0, 2000)
+    big = _batch(r, 0, 30000)
+    need_small = mt.workspace_bytes(ix, len(small[0]), 2000, 150, **prm)
+    need_big = mt.workspace_bytes(ix, len(big[0]), 30000, 150, **prm)
+    budget = need_small + need_small // 5                # too small for any slot plan
+    assert need_big > budget
+    srv = mt.Server(ix, hbm_budget=budget, max_slots=2, **prm)
+    rid_big = srv.submit(*big)
+    rid_small = srv.submit(*small)
+    rc, _, _ = srv.poll(rid_big, 120_000)
+    assert rc == mt.MT_ENOMEM
+    rc, _, out = srv.poll(rid_small, 120_000)
+    assert rc == mt.MT_OK
+    _same(out, mt.classify(ix, *small, **prm))
+    srv.close()
+
+
+def test_cancel_and_bounded_poll(mt, work):
+    c, g, r, ix, prm = work
+    need = mt.workspace_bytes(ix, 30000 * 150, 30000, 150, **prm)
+    srv = mt.Server(ix, hbm_budget=need + need // 2, max_slots=1, **prm)   # one at a time, no plan
+    ids = [srv.submit(*_batch(r, 0, 30000)) for _ in range(4)]
+    assert srv.cancel(ids[-1]) == mt.MT_OK
+    rc, _, _ = srv.poll(ids[-1], 0)
+    assert rc == mt.MT_ECANCELED
+    for rid in ids[:-1]:
+        rc, _, out = srv.poll(rid, 120_000)
+        assert rc == mt.MT_OK
+    assert srv.cancel(ids[0]) == mt.MT_EBUSY              # already done
+    srv.close()

@@ -590,3 +590,20 @@ def test_window_does_not_run_into_the_next_genome(oracle_lib):
         W = [gs[0][ws + x] if 0 <= ws + x < len(gs[0]) else "A" for x in range(len(read) + 2 * E)]
         obst = np.array([not (0 <= ws + x < len(gs[0])) for x in range(len(read) + 2 * E)])
         assert top["dist"] == _greedy_by_dp(_map(read, "".join(W), E, obst), E) >= 1
+
+
+def test_threaded_index_build_is_identical(oracle_lib):
+    """The threaded build used for large verification runs gives the single-threaded index."""
+    c = gen.config(2, n_genomes=30, genome_len=20_000, n_reads=2000)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    a = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    b = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"], threads=5)
+    assert a.n_occ == b.n_occ
+    p = oracle.params(e_abs=8, e_permille=0, min_seeds=3)
+    ra, rb = oracle.classify(a, r.seq, r.offsets, p), oracle.classify(b, r.seq, r.offsets, p)
+    for key in ("taxon", "nloc", "genome_hits", "U"):
+        assert np.array_equal(ra[key], rb[key])
+    assert np.array_equal(ra["locs"], rb["locs"])
+    for code in np.unique(oracle.minimizers(g.genome(3), c["k"], c["w"], 1)[0])[:200]:
+        assert [x.tolist() for x in a.lookup(int(code))] == [x.tolist() for x in b.lookup(int(code))]
