@@ -48,16 +48,23 @@ struct WarpSmem {
     uint64_t rd[RDW];           // packed read
     uint64_t key[KEYS];         // k-mer keys of the tile
     uint64_t hits[HCAP];        // seed-match keys
-    uint64_t inl[32 * 3];       // inline occurrences of the 32 lookups in flight
-    uint64_t off[32];           // occurrence-list offsets of the lookups in flight
-    uint32_t pref[33];          // exclusive prefix of match counts of the lookups in flight
-    uint32_t meta[32];          // rpos | strand << 16 | ninline << 17
     uint16_t mpos[TILE];        // minimizer positions of the tile
-    uint16_t gs[HCAP + 1];      // starts of (genome, strand) groups in the sorted matches
-    uint16_t qs[HCAP];          // qualifying locations: first match
-    uint16_t qn[HCAP];          //                       seed count
-    uint32_t qcount;
+    union {                     // lookups (per tile) and location walk (per read) never overlap
+        struct {
+            uint64_t inl[32 * 3];   // inline occurrences of the 32 lookups in flight
+            uint64_t off[32];       // occurrence-list offsets of the lookups in flight
+            uint32_t pref[33];      // exclusive prefix of match counts of the lookups in flight
+            uint32_t meta[32];      // rpos | strand << 16 | ninline << 17
+        } pr;
+        struct {
+            uint16_t gs[HCAP + 1];  // starts of (genome, strand) groups in the sorted matches
+            uint16_t qs[HCAP];      // qualifying locations: first match
+            uint16_t qn[HCAP];      //                       seed count
+            uint32_t qcount;
+        } wk;
+    } u;
 };
+
 enum StatIdx { ST_MINS = 0, ST_HITS, ST_CAND, ST_ACC, ST_MULTI, ST_FB, ST_EXT, ST_STORED, ST_N };
 
 struct Counters {
@@ -161,8 +168,8 @@ MT_DEV uint32_t lower_bound_u64(const uint64_t *a, uint32_t lo, uint32_t hi, uin
 
 // Bitonic sort of 32*R keys held in registers: element r*32 + lane in v[r]. Exchanges across
 // lanes use shuffles, exchanges across register slots stay in the lane.
-template <int R>
-MT_DEV void bitonic_regs(uint64_t (&v)[R]) {
+template <int R, typename T>
+MT_DEV void bitonic_regs(T (&v)[R]) {
     const uint32_t lane = lane_id();
     constexpr uint32_t P = 32u * R;
 #pragma unroll
@@ -176,7 +183,7 @@ MT_DEV void bitonic_regs(uint64_t (&v)[R]) {
                     if (pr > r) {
                         const uint32_t i = (uint32_t)r * 32u + lane;
                         const bool up = (i & k) == 0;
-                        const uint64_t a = v[r], b = v[pr];
+                        const T a = v[r], b = v[pr];
                         const bool sw = (a > b) == up;
                         v[r] = sw ? b : a;
                         v[pr] = sw ? a : b;
@@ -186,7 +193,7 @@ MT_DEV void bitonic_regs(uint64_t (&v)[R]) {
 #pragma unroll
                 for (int r = 0; r < R; r++) {
                     const uint32_t i = (uint32_t)r * 32u + lane;
-                    const uint64_t o = __shfl_xor_sync(FULL, v[r], j);
+                    const T o = __shfl_xor_sync(FULL, v[r], j);
                     const bool up = (i & k) == 0;
                     const bool lower = (lane & j) == 0;
                     v[r] = (lower == up) ? (v[r] < o ? v[r] : o) : (v[r] < o ? o : v[r]);
@@ -205,11 +212,40 @@ MT_DEV void sort_hits_R(uint64_t *h, uint32_t H) {
         uint32_t i = (uint32_t)r * 32u + lane;
         v[r] = i < H ? h[i] : ~0ull;
     }
-    bitonic_regs<R>(v);
+    bitonic_regs<R, uint64_t>(v);
 #pragma unroll
     for (int r = 0; r < R; r++) {
         uint32_t i = (uint32_t)r * 32u + lane;
         if (i < H) h[i] = v[r];
+    }
+    __syncwarp();
+}
+
+// The same sort on 32-bit keys genome | strand | diagonal + bias, when the index's genome count
+// and lengths fit them (order-preserving, so the expanded result is the sorted 64-bit keys).
+template <int R>
+MT_DEV void sort_hits32_R(uint64_t *h, uint32_t H, uint32_t db) {
+    const uint32_t lane = lane_id();
+    const uint64_t lowmask = (1ull << db) - 1;
+    uint32_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const uint32_t i = (uint32_t)r * 32u + lane;
+        uint32_t c = 0xFFFFFFFFu;
+        if (i < H) {
+            const uint64_t x = h[i];
+            c = (uint32_t)(((x >> 34) << (db + 1)) | (((x >> 33) & 1u) << db) | (x & lowmask));
+        }
+        v[r] = c;
+    }
+    bitonic_regs<R, uint32_t>(v);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const uint32_t i = (uint32_t)r * 32u + lane;
+        if (i < H) {
+            const uint64_t c = v[r];
+            h[i] = ((c >> (db + 1)) << 34) | (((c >> db) & 1u) << 33) | (c & lowmask);
+        }
     }
     __syncwarp();
 }
@@ -232,9 +268,12 @@ MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
 }
 
 // Up to 64 matches are sorted in registers; the rare larger sets in shared memory.
-MT_DEV void sort_hits(uint64_t *h, uint32_t H) {
-    if (H <= 32) sort_hits_R<1>(h, H);
-    else if (H <= 64) sort_hits_R<2>(h, H);
+template <bool HK32>
+MT_DEV void sort_hits(uint64_t *h, uint32_t H, uint32_t db) {
+    if (HK32 && H <= 32) sort_hits32_R<1>(h, H, db);
+    else if (HK32 && H <= 64) sort_hits32_R<2>(h, H, db);
+    else if (!HK32 && H <= 32) sort_hits_R<1>(h, H);
+    else if (!HK32 && H <= 64) sort_hits_R<2>(h, H);
     else {
         uint32_t P = 128;
         while (P < H) P <<= 1;
@@ -251,7 +290,7 @@ MT_DEV void read_kmer_at(const uint64_t *rd, uint32_t p, uint32_t k, uint32_t ca
     canon(fwd, rc, canonical, code, strand);
 }
 
-template <bool SMEM_HIST>
+template <bool SMEM_HIST, bool HK32>
 __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(smraw);
@@ -407,23 +446,23 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
                             cnt = ni ? ni : (uint32_t)(a.y >> 40);
                             if (ni > 1) {
                                 const ulonglong2 b2 = __ldg(&A.ix.table[2 * s + 1]);
-                                ws.inl[lane * 3 + 1] = b2.x;
-                                ws.inl[lane * 3 + 2] = b2.y;
+                                ws.u.pr.inl[lane * 3 + 1] = b2.x;
+                                ws.u.pr.inl[lane * 3 + 2] = b2.y;
                             }
                             break;
                         }
                         s = (s + 1) & A.ix.slot_mask;
                     }
                     if (cnt > A.max_occ) cnt = 0;
-                    ws.inl[lane * 3] = w1;
-                    ws.off[lane] = w1 & OFF_MASK40;
-                    ws.meta[lane] = p | (st << 16) | (ni << 17);
+                    ws.u.pr.inl[lane * 3] = w1;
+                    ws.u.pr.off[lane] = w1 & OFF_MASK40;
+                    ws.u.pr.meta[lane] = p | (st << 16) | (ni << 17);
                     if (!ni) n_ext += cnt;
                 }
                 const uint32_t incl = warp_incl_scan(cnt);
                 const uint32_t total = __shfl_sync(FULL, incl, 31);
-                ws.pref[lane] = incl - cnt;
-                if (lane == 31) ws.pref[32] = incl;
+                ws.u.pr.pref[lane] = incl - cnt;
+                if (lane == 31) ws.u.pr.pref[32] = incl;
                 if (!ovf && H + total > HCAP) {
                     // switch to counting only: count what is buffered so far
                     for (uint32_t i = lane; i < H; i += 32) atomicAdd(&H_out[hk_genome(ws.hits[i])], 1ull);
@@ -435,11 +474,11 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
                     uint32_t lo = 0, hi = nl;   // owner: last lookup with pref <= q
                     while (hi - lo > 1) {
                         uint32_t mid = (lo + hi) >> 1;
-                        if (ws.pref[mid] <= q) lo = mid; else hi = mid;
+                        if (ws.u.pr.pref[mid] <= q) lo = mid; else hi = mid;
                     }
-                    const uint32_t t = q - ws.pref[lo];
-                    const uint32_t meta = ws.meta[lo];
-                    const uint64_t occ = (meta >> 17) ? ws.inl[lo * 3 + t] : __ldg(&A.ix.occ[ws.off[lo] + t]);
+                    const uint32_t t = q - ws.u.pr.pref[lo];
+                    const uint32_t meta = ws.u.pr.meta[lo];
+                    const uint64_t occ = (meta >> 17) ? ws.u.pr.inl[lo * 3 + t] : __ldg(&A.ix.occ[ws.u.pr.off[lo] + t]);
                     if (!ovf) ws.hits[H + q] = hit_key(occ, meta & 0xFFFFu, (meta >> 16) & 1u, n, k);
                     else atomicAdd(&H_out[occ >> 33], 1ull);
                 }
@@ -460,44 +499,44 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             if (lane == 0) A.qcnt[r] = 0;
             continue;
         }
-        sort_hits(ws.hits, H);
+        sort_hits<HK32>(ws.hits, H, A.ix.hk_db);
         // (genome, strand) groups of the sorted matches, in order
         uint32_t ng = 0;
         for (uint32_t i0 = 0; i0 < H; i0 += 32) {
             const uint32_t i = i0 + lane;
             const bool st = i < H && (i == 0 || (ws.hits[i] >> 33) != (ws.hits[i - 1] >> 33));
             const unsigned bal = __ballot_sync(FULL, st);
-            if (st) ws.gs[ng + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)i;
+            if (st) ws.u.wk.gs[ng + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)i;
             ng += __popc(bal);
         }
-        if (lane == 0) { ws.gs[ng] = (uint16_t)H; ws.qcount = 0; }
+        if (lane == 0) { ws.u.wk.gs[ng] = (uint16_t)H; ws.u.wk.qcount = 0; }
         __syncwarp();
         // containment counts (one atomic per group) and greedy locations per group: a
         // location starting at match s ends before the first match with key >= key_s + E + 1
         for (uint32_t gi = lane; gi < ng; gi += 32) {
-            uint32_t s = ws.gs[gi];
-            const uint32_t ge = ws.gs[gi + 1];
+            uint32_t s = ws.u.wk.gs[gi];
+            const uint32_t ge = ws.u.wk.gs[gi + 1];
             atomicAdd(&H_out[hk_genome(ws.hits[s])], (unsigned long long)(ge - s));
             while (s < ge) {
                 const uint32_t e = lower_bound_u64(ws.hits, s + 1, ge, ws.hits[s] + E + 1);
                 if (e - s >= A.min_seeds) {
-                    const uint32_t qi = atomicAdd(&ws.qcount, 1u);
-                    ws.qs[qi] = (uint16_t)s;
-                    ws.qn[qi] = (uint16_t)(e - s);
+                    const uint32_t qi = atomicAdd(&ws.u.wk.qcount, 1u);
+                    ws.u.wk.qs[qi] = (uint16_t)s;
+                    ws.u.wk.qn[qi] = (uint16_t)(e - s);
                 }
                 s = e;
             }
         }
         __syncwarp();
-        const uint32_t Q = ws.qcount;
+        const uint32_t Q = ws.u.wk.qcount;
         // rank the qualifying locations: seeds descending, then (genome, strand, diagonal)
         for (uint32_t qi = lane; qi < Q; qi += 32) {
-            const uint32_t seeds_i = ws.qn[qi];
-            const uint64_t hk_i = ws.hits[ws.qs[qi]];
+            const uint32_t seeds_i = ws.u.wk.qn[qi];
+            const uint64_t hk_i = ws.hits[ws.u.wk.qs[qi]];
             uint32_t rank = 0;
             for (uint32_t qj = 0; qj < Q; qj++) {
-                const uint32_t seeds_j = ws.qn[qj];
-                const uint64_t hk_j = ws.hits[ws.qs[qj]];
+                const uint32_t seeds_j = ws.u.wk.qn[qj];
+                const uint64_t hk_j = ws.hits[ws.u.wk.qs[qj]];
                 rank += (seeds_j > seeds_i) || (seeds_j == seeds_i && hk_j < hk_i);
             }
             if (rank < CSTORE) {
@@ -749,46 +788,69 @@ __global__ void k_decide(DecideArgs A) {
         int32_t uniq = -1;
         bool is_multi = false;
         if (r < io.n_reads) {
-            uint32_t n = (uint32_t)(io.roff[r + 1] - io.roff[r]);
-            uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
-            uint32_t nl = A.nloc_ws[r];
+            const uint32_t n = (uint32_t)(io.roff[r + 1] - io.roff[r]);
+            const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
+            const uint32_t nl = A.nloc_ws[r];
+            const uint32_t tn = A.top_n;
             cand += nl;
+            // every loop below runs over the at most MT_MAX_TOPN slots with static indices
+            uint32_t d[MT_MAX_TOPN];
+            Cluster cl[MT_MAX_TOPN];
             uint32_t best = E + 1;
-            for (uint32_t t = 0; t < nl; t++) {
-                uint32_t d = A.dist[r * A.top_n + t];
-                if (d <= E && d < best) best = d;
+#pragma unroll
+            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+                d[t] = 0xFFu;
+                cl[t].hkey = 0; cl[t].seeds = 0; cl[t].pad = 0;
+                if (t < nl) {
+                    d[t] = A.dist[r * tn + t];
+                    cl[t] = A.cand[r * tn + t];
+                    if (d[t] <= E && d[t] < best) best = d[t];
+                }
             }
             int32_t tax = -1;
             int32_t S[MT_MAX_TOPN];
             uint32_t ns = 0;
-            for (uint32_t t = 0; t < A.top_n; t++) {
-                mt_loc L;
-                memset(&L, 0, sizeof(L));
-                L.genome = -1;
-                if (t < nl) {
-                    Cluster c = A.cand[r * A.top_n + t];
-                    uint32_t d = A.dist[r * A.top_n + t];
-                    int32_t g = (int32_t)hk_genome(c.hkey);
-                    L.wstart = hk_diag(c.hkey) - (int64_t)E;
-                    L.genome = g;
-                    L.seeds = c.seeds;
-                    L.strand = (uint8_t)hk_rel(c.hkey);
-                    L.dist = (uint8_t)d;
-                    if (best <= E && d == best) {
-                        if (tax < 0) tax = g;
-                        bool seen = false;
-                        for (uint32_t q = 0; q < ns; q++) seen |= (S[q] == g);
-                        if (!seen) S[ns++] = g;
-                    }
+#pragma unroll
+            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+                S[t] = -1;
+                if (t < nl && best <= E && d[t] == best) {
+                    const int32_t g = (int32_t)hk_genome(cl[t].hkey);
+                    if (tax < 0) tax = g;
+                    bool seen = false;
+#pragma unroll
+                    for (uint32_t q = 0; q < t; q++) seen |= (S[q] == g);
+                    if (!seen) { S[t] = g; ns++; }
                 }
-                if (io.locs) io.locs[r * A.top_n + t] = L;
+            }
+#pragma unroll
+            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+                if (t < tn && io.locs) {
+                    mt_loc L;
+                    memset(&L, 0, sizeof(L));
+                    L.genome = -1;
+                    if (t < nl) {
+                        L.wstart = hk_diag(cl[t].hkey) - (int64_t)E;
+                        L.genome = (int32_t)hk_genome(cl[t].hkey);
+                        L.seeds = cl[t].seeds;
+                        L.strand = (uint8_t)hk_rel(cl[t].hkey);
+                        L.dist = (uint8_t)d[t];
+                    }
+                    io.locs[r * tn + t] = L;
+                }
             }
             io.taxon[r] = tax;
             if (io.nloc) io.nloc[r] = (uint8_t)nl;
-            if (ns == 1) uniq = S[0];
+            if (ns == 1) uniq = tax;
             if (ns >= 2) {
                 is_multi = true;
-                for (uint32_t q = 0; q < A.top_n; q++) A.multi_set[r * A.top_n + q] = q < ns ? S[q] : -1;
+                // the distinct genomes at the best distance, in rank order, then -1
+                uint32_t o = 0;
+#pragma unroll
+                for (uint32_t t = 0; t < MT_MAX_TOPN; t++)
+                    if (S[t] >= 0) { A.multi_set[r * tn + o] = S[t]; o++; }
+#pragma unroll
+                for (uint32_t t = 0; t < MT_MAX_TOPN; t++)
+                    if (t >= o && t < tn) A.multi_set[r * tn + t] = -1;
             }
             acc += (best <= E);
             mul += is_multi;
@@ -969,6 +1031,18 @@ struct EnqueueCtx {
     uint64_t launches;
 };
 
+template <bool SH, bool HK32>
+static int launch_seed(const SeedArgs &A, size_t smem, uint64_t need, cudaStream_t s) {
+    MT_CK(cudaFuncSetAttribute(k_seed<SH, HK32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<SH, HK32>, SEED_THREADS, smem));
+    per_sm = std::max(per_sm, 1);
+    const unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
+    k_seed<SH, HK32><<<grid, SEED_THREADS, smem, s>>>(A);
+    MT_CK(cudaGetLastError());
+    return MT_OK;
+}
+
 static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
     const Layout &L = *c.L;
     const mt_classify_params *p = c.p;
@@ -999,21 +1073,12 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         A.fb_list = (uint32_t *)P(L.fb_list);
         A.ctr = ctr;
         const bool smem_hist = G <= SMEM_HIST_MAX;
+        const bool hk32 = ix->hk_db != 0;
         const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem);
-        int per_sm = 0;
-        if (smem_hist) {
-            MT_CK(cudaFuncSetAttribute(k_seed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<true>, SEED_THREADS, smem));
-        } else {
-            MT_CK(cudaFuncSetAttribute(k_seed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<false>, SEED_THREADS, smem));
-        }
-        per_sm = std::max(per_sm, 1);
         const uint64_t need = (c.cap_reads + SEED_WARPS - 1) / SEED_WARPS;
-        const unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
-        if (smem_hist) k_seed<true><<<grid, SEED_THREADS, smem, s>>>(A);
-        else k_seed<false><<<grid, SEED_THREADS, smem, s>>>(A);
-        MT_CK(cudaGetLastError());
+        int rc = hk32 ? (smem_hist ? launch_seed<true, true>(A, smem, need, s) : launch_seed<false, true>(A, smem, need, s))
+                      : (smem_hist ? launch_seed<true, false>(A, smem, need, s) : launch_seed<false, false>(A, smem, need, s));
+        if (rc) return rc;
         mark(1);
 
         k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
@@ -1040,7 +1105,7 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         MT_CK(cudaGetLastError());
         mark(2);
 
-        int rc = launch_classify_eda(iv, A.rw, io, (const uint32_t *)P(L.cl), &ctr->cl_count, c.cap_reads * top_n,
+        rc = launch_classify_eda(iv, A.rw, io, (const uint32_t *)P(L.cl), &ctr->cl_count, c.cap_reads * top_n,
                                      (const Cluster *)P(L.cand), top_n, p->e_abs, p->e_permille, c.maxn, c.maxE,
                                      p->eda_mode, (uint8_t *)P(L.dist), &ctr->eda_counter, s, c.allow_tune);
         if (rc) return rc;

@@ -102,7 +102,8 @@ struct IndexView {
     const uint64_t *ref;        // packed genomes
     const uint64_t *gword;      // first word of genome g in ref
     const uint64_t *glen;       // genome lengths (bases)
-    uint32_t k, w, canonical, pad;
+    uint32_t k, w, canonical;
+    uint32_t hk_db;             // diagonal bits of 32-bit match keys (0: keys need 64 bits)
 };
 
 MT_DEV Lookup probe(const IndexView &ix, uint64_t code, uint64_t key, uint32_t *err) {

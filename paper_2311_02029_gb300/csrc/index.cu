@@ -255,6 +255,14 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t 
         hgword[g] = (hoff[g] >> 5) + g;
     }
     ix->ref_words = (total >> 5) + G + 1;
+    {   // 32-bit match keys (genome | strand | diagonal + bias) when they fit
+        uint64_t max_len = 0;
+        for (uint32_t g = 0; g < G; g++) max_len = std::max<uint64_t>(max_len, ix->h_glen[g]);
+        uint32_t db = 1, gb = 1;
+        while ((1ull << db) <= max_len + DIAG_BIAS + MT_MAX_E + 2) db++;
+        while ((1ull << gb) < G) gb++;
+        ix->hk_db = (gb + 1 + db <= 32) ? db : 0;
+    }
 
     int rc = MT_OK;
     uint8_t *d_seq = nullptr;

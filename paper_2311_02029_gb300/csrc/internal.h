@@ -45,6 +45,7 @@ struct mt_index {
     uint32_t G = 0, k = 0, w = 0, canonical = 0;
     uint64_t total_bases = 0, n_occ = 0, n_keys = 0, slots = 0;
     uint32_t slot_shift = 0;
+    uint32_t hk_db = 0;          // diagonal bits of 32-bit match keys; 0 if they do not fit
     uint64_t ref_words = 0;
     uint64_t *d_ref = nullptr, *d_gword = nullptr, *d_glen = nullptr, *d_occ = nullptr;
     ulonglong2 *d_table = nullptr;
@@ -61,7 +62,7 @@ struct mt_index {
         v.ref = d_ref;
         v.gword = d_gword;
         v.glen = d_glen;
-        v.k = k; v.w = w; v.canonical = canonical; v.pad = 0;
+        v.k = k; v.w = w; v.canonical = canonical; v.hk_db = hk_db;
         return v;
     }
 };
