@@ -44,21 +44,25 @@ static constexpr uint32_t SMEM_HIST_MAX = 4096;           // genomes counted in 
 static constexpr int FB_CTAS = 16;
 static constexpr int FB_THREADS = 256;
 
+// Per-warp shared memory of the seeding kernel. HitT is the seed-match key: 32 bits when the
+// index's genome count and lengths allow (see HitKey), else 64.
+template <typename HitT>
 struct WarpSmem {
-    uint64_t rd[RDW];           // packed read
-    uint64_t key[KEYS];         // k-mer keys of the tile
-    uint64_t hits[HCAP];        // seed-match keys
-    uint16_t mpos[TILE];        // minimizer positions of the tile
-    union {                     // lookups (per tile) and location walk (per read) never overlap
+    uint64_t rd[RDW];               // packed read
+    HitT hits[HCAP];                // seed-match keys of the read
+    union {                         // the tiles of a read, then its location walk
         struct {
-            uint64_t inl[32 * 3];   // inline occurrences of the 32 lookups in flight
-            uint64_t off[32];       // occurrence-list offsets of the lookups in flight
-            uint32_t pref[33];      // exclusive prefix of match counts of the lookups in flight
-            uint32_t meta[32];      // rpos | strand << 16 | ninline << 17
-        } pr;
+            uint64_t key[KEYS];     // k-mer keys of the tile
+            uint64_t code[KEYS];    // canonical code | strand << 63
+            uint16_t mpos[TILE];    // minimizer positions of the tile
+            // lookups of one round, by rank among those with matches
+            uint64_t e_w[32 * 3];   // inline occurrences, or the occurrence-list offset
+            uint32_t e_pre[32];     // first match of the lookup within the round
+            uint32_t e_meta[32];    // rpos | strand << 16 | inline << 17
+        } t;
         struct {
             uint16_t gs[HCAP + 1];  // starts of (genome, strand) groups in the sorted matches
-            uint16_t qs[HCAP];      // qualifying locations: first match
+            HitT qk[HCAP];          // qualifying locations: key of the first match
             uint16_t qn[HCAP];      //                       seed count
             uint32_t qcount;
         } wk;
@@ -93,78 +97,120 @@ struct SeedArgs {
 
 // ---- read packing (one warp) ------------------------------------------------------------
 // Four bytes at a time: code = ((b >> 1) & 3) with G/T swapped; a byte is valid iff the
-// ASCII letter of its code (picked with a byte permute from "ACGT") equals the byte.
-MT_DEV uint32_t swar_pack4(uint32_t u, uint32_t inmask, bool &bad) {
+// ASCII letter of its code (picked with a byte permute from "ACGT") equals the byte. Bytes
+// outside `m` give code 0 and are not checked. Returns the four codes as 8 bits, first byte
+// lowest (one multiply gathers the 2-bit fields: the partial products never overlap).
+MT_DEV uint32_t swar_pack4(uint32_t u, uint32_t m, bool &bad) {
     uint32_t c = (u >> 1) & 0x03030303u;
     c ^= (c >> 1) & 0x01010101u;
-    c &= inmask;
-    uint32_t sel = (c & 0x3u) | ((c >> 4) & 0x30u) | ((c >> 8) & 0x300u) | ((c >> 12) & 0x3000u);
-    uint32_t exp = __byte_perm(0x54474341u, 0u, sel);
-    bad |= ((exp ^ u) & inmask) != 0u;
-    return (c & 0x3u) | ((c >> 6) & 0xCu) | ((c >> 12) & 0x30u) | ((c >> 18) & 0xC0u);
+    c &= m;
+    const uint32_t t = c | (c >> 4);
+    const uint32_t sel = (t & 0xFFu) | ((t >> 8) & 0xFF00u);     // code of byte i in nibble i
+    bad |= ((__byte_perm(0x54474341u, 0u, sel) ^ u) & m) != 0u;
+    return (c * 0x01041040u) >> 24;
 }
 
-MT_DEV uint32_t byte_mask(int64_t lo, int64_t hi) {   // bytes [lo, hi) of a 4-byte word
-    lo = lo < 0 ? 0 : lo;
-    hi = hi > 4 ? 4 : hi;
-    if (hi <= lo) return 0u;
-    uint32_t m_hi = hi >= 4 ? 0xFFFFFFFFu : ((1u << (8 * hi)) - 1u);
-    uint32_t m_lo = (1u << (8 * lo)) - 1u;
-    return m_hi & ~m_lo;
+// Bytes [0, nb) of a 4-byte word, nb clamped to [0, 4].
+MT_DEV uint32_t low_bytes(int32_t nb) {
+    return nb >= 4 ? 0xFFFFFFFFu : nb <= 0 ? 0u : ((1u << (8 * nb)) - 1u);
 }
 
+// Packs bases [start, start + n) of `reads` into rd[0, nw) (2 bits a base, base i at bits
+// 2(i%32) of word i/32, the tail of the last word zero) and into `dst`, and zeroes rd[nw],
+// rd[nw + 1]. Each lane converts 8 bases a pass from two aligned 8-byte loads; four lanes
+// assemble one word with two shuffles. Returns true (on every lane) if a byte is not ACGT.
 MT_DEV bool warp_pack(const uint8_t *reads, uint64_t n_bases, int vec_ok, uint64_t start, uint32_t n,
-                      uint64_t *rd) {
+                      uint64_t *rd, uint64_t *dst) {
     const uint32_t lane = lane_id();
     const uint32_t nw = (n + 31) / 32;
-    for (uint32_t i = lane; i < nw + 2; i += 32) rd[i] = 0;
-    __syncwarp();
-    const uint64_t A = start & ~15ull, end = start + n;
-    const uint32_t nch = (uint32_t)((end - A + 15) >> 4);
+    const uint32_t sh = (uint32_t)(start & 7u) * 8u;
+    const uint64_t a0 = start & ~7ull;
     bool bad = false;
-    for (uint32_t c = lane; c < nch; c += 32) {
-        const uint64_t cb = A + 16ull * c;
-        uint32_t u[4];
-        if (vec_ok && cb + 16 <= n_bases) {
-            uint4 v = __ldg(reinterpret_cast<const uint4 *>(reads + cb));
-            u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                uint32_t x = 0;
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    uint64_t pos = cb + 4 * q + b;
-                    uint32_t by = (pos >= start && pos < end) ? reads[pos] : 'A';
-                    x |= by << (8 * b);
+    __syncwarp();                                 // rd of the previous read is no longer read
+    for (uint32_t b0 = 0; b0 < n; b0 += 256) {
+        const uint32_t j = b0 + 8 * lane;         // first base of this lane
+        uint32_t c16 = 0;
+        if (j < n) {
+            uint32_t x0, x1;
+            const uint64_t a = a0 + j;            // aligned: bases start + j .. + 7 lie in [a, a + 16)
+            if (vec_ok && a + 16 <= n_bases) {
+                const uint2 lo = __ldg(reinterpret_cast<const uint2 *>(reads + a));
+                const uint2 hi = __ldg(reinterpret_cast<const uint2 *>(reads + a + 8));
+                if (sh < 32) {
+                    x0 = __funnelshift_r(lo.x, lo.y, sh);
+                    x1 = __funnelshift_r(lo.y, hi.x, sh);
+                } else {
+                    x0 = __funnelshift_r(lo.y, hi.x, sh - 32);
+                    x1 = __funnelshift_r(hi.x, hi.y, sh - 32);
                 }
-                u[q] = x;
-            }
-        }
-        uint32_t c32 = 0;
+            } else {
+                x0 = x1 = 0;
+                const uint64_t p0 = start + j, end = start + n;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            int64_t wb = (int64_t)(cb + 4 * q);
-            uint32_t m = byte_mask((int64_t)start - wb, (int64_t)end - wb);
-            c32 |= swar_pack4(u[q], m, bad) << (8 * q);
+                for (int q = 0; q < 8; q++) {
+                    const uint32_t by = (p0 + q < end) ? reads[p0 + q] : 'A';
+                    if (q < 4) x0 |= by << (8 * q); else x1 |= by << (8 * (q - 4));
+                }
+            }
+            const int32_t nb = (int32_t)(n - j);
+            c16 = swar_pack4(x0, low_bytes(nb), bad) | (swar_pack4(x1, low_bytes(nb - 4), bad) << 8);
         }
-        int64_t j0 = (int64_t)cb - (int64_t)start;
-        if (j0 < 0) { c32 >>= (uint32_t)(2 * (-j0)); j0 = 0; }
-        uint32_t wi = (uint32_t)(j0 >> 5), o = (uint32_t)(2 * (j0 & 31));
-        atomicOr(reinterpret_cast<unsigned long long *>(&rd[wi]), (unsigned long long)c32 << o);
-        if (o > 32) atomicOr(reinterpret_cast<unsigned long long *>(&rd[wi + 1]), (unsigned long long)c32 >> (64 - o));
+        uint32_t v = c16 << (16 * (lane & 1u));
+        v |= __shfl_xor_sync(FULL, v, 1);
+        const uint32_t hi = __shfl_xor_sync(FULL, v, 2);
+        const uint32_t t = (b0 >> 5) + (lane >> 2);
+        if ((lane & 3u) == 0 && t < nw) {
+            const uint64_t word = (uint64_t)v | ((uint64_t)hi << 32);
+            rd[t] = word;
+            dst[t] = word;
+        }
     }
+    if (lane < 2) rd[nw + lane] = 0;
     __syncwarp();
     return __any_sync(FULL, bad);
 }
 
-MT_DEV uint32_t lower_bound_u64(const uint64_t *a, uint32_t lo, uint32_t hi, uint64_t key) {
+template <typename T>
+MT_DEV uint32_t lower_bound_t(const T *a, uint32_t lo, uint32_t hi, T key) {
     while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
         if (a[mid] < key) lo = mid + 1; else hi = mid;
     }
     return lo;
 }
+
+// Seed-match keys in the seeding kernel. Both forms order matches by (genome, relative
+// strand, diagonal); the 32-bit form packs genome << (db + 1) | rel << db | diag + bias and
+// is used when the index guarantees those fields fit (bias + diagonal + E + 1 < 2^db too,
+// so a band bound key + E + 1 never leaves its (genome, strand) group).
+template <bool HK32> struct HitKey;
+template <> struct HitKey<true> {
+    using T = uint32_t;
+    uint32_t db;
+    MT_DEV T make(uint64_t occ, uint32_t rpos, uint32_t rst, uint32_t nk) const {
+        const uint32_t rel = ((uint32_t)occ & 1u) ^ rst;
+        const uint32_t rp = rel ? nk - rpos : rpos;
+        return ((uint32_t)(occ >> 33) << (db + 1)) | (rel << db) | ((uint32_t)(occ >> 1) + DIAG_BIAS - rp);
+    }
+    MT_DEV uint32_t grel(T h) const { return h >> db; }
+    MT_DEV uint32_t genome(T h) const { return h >> (db + 1); }
+    MT_DEV uint64_t wide(T h) const {
+        return ((uint64_t)(h >> (db + 1)) << 34) | ((uint64_t)((h >> db) & 1u) << 33) | (h & ((1u << db) - 1u));
+    }
+};
+template <> struct HitKey<false> {
+    using T = uint64_t;
+    uint32_t db;
+    MT_DEV T make(uint64_t occ, uint32_t rpos, uint32_t rst, uint32_t nk) const {
+        const uint32_t rel = ((uint32_t)occ & 1u) ^ rst;
+        const int64_t rp = rel ? (int64_t)(nk - rpos) : (int64_t)rpos;
+        const int64_t diag = (int64_t)((occ >> 1) & 0xFFFFFFFFull) - rp;
+        return ((occ >> 33) << 34) | ((uint64_t)rel << 33) | (uint64_t)(diag + DIAG_BIAS);
+    }
+    MT_DEV uint64_t grel(T h) const { return h >> 33; }
+    MT_DEV uint32_t genome(T h) const { return (uint32_t)(h >> 34); }
+    MT_DEV uint64_t wide(T h) const { return h; }
+};
 
 // Bitonic sort of 32*R keys held in registers: element r*32 + lane in v[r]. Exchanges across
 // lanes use shuffles, exchanges across register slots stay in the lane.
@@ -203,55 +249,27 @@ MT_DEV void bitonic_regs(T (&v)[R]) {
     }
 }
 
-template <int R>
-MT_DEV void sort_hits_R(uint64_t *h, uint32_t H) {
+template <int R, typename T>
+MT_DEV void sort_regs(T *h, uint32_t H) {
     const uint32_t lane = lane_id();
-    uint64_t v[R];
+    T v[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        uint32_t i = (uint32_t)r * 32u + lane;
-        v[r] = i < H ? h[i] : ~0ull;
+        const uint32_t i = (uint32_t)r * 32u + lane;
+        v[r] = i < H ? h[i] : (T)~(T)0;
     }
-    bitonic_regs<R, uint64_t>(v);
+    bitonic_regs<R, T>(v);
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        uint32_t i = (uint32_t)r * 32u + lane;
+        const uint32_t i = (uint32_t)r * 32u + lane;
         if (i < H) h[i] = v[r];
     }
     __syncwarp();
 }
 
-// The same sort on 32-bit keys genome | strand | diagonal + bias, when the index's genome count
-// and lengths fit them (order-preserving, so the expanded result is the sorted 64-bit keys).
-template <int R>
-MT_DEV void sort_hits32_R(uint64_t *h, uint32_t H, uint32_t db) {
-    const uint32_t lane = lane_id();
-    const uint64_t lowmask = (1ull << db) - 1;
-    uint32_t v[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const uint32_t i = (uint32_t)r * 32u + lane;
-        uint32_t c = 0xFFFFFFFFu;
-        if (i < H) {
-            const uint64_t x = h[i];
-            c = (uint32_t)(((x >> 34) << (db + 1)) | (((x >> 33) & 1u) << db) | (x & lowmask));
-        }
-        v[r] = c;
-    }
-    bitonic_regs<R, uint32_t>(v);
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const uint32_t i = (uint32_t)r * 32u + lane;
-        if (i < H) {
-            const uint64_t c = v[r];
-            h[i] = ((c >> (db + 1)) << 34) | (((c >> db) & 1u) << 33) | (c & lowmask);
-        }
-    }
-    __syncwarp();
-}
-
 // warp bitonic sort of a[0, P) in shared memory, P a power of two >= 2
-MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
+template <typename T>
+MT_DEV void warp_bitonic(T *a, uint32_t P) {
     const uint32_t lane = lane_id();
     for (uint32_t k = 2; k <= P; k <<= 1) {
         for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -259,7 +277,7 @@ MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
                 uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
                 uint32_t hi = lo + j;
                 bool up = (lo & k) == 0;
-                uint64_t x = a[lo], y = a[hi];
+                T x = a[lo], y = a[hi];
                 if ((x > y) == up) { a[lo] = y; a[hi] = x; }
             }
             __syncwarp();
@@ -267,43 +285,37 @@ MT_DEV void warp_bitonic(uint64_t *a, uint32_t P) {
     }
 }
 
-// Up to 64 matches are sorted in registers; the rare larger sets in shared memory.
-template <bool HK32>
-MT_DEV void sort_hits(uint64_t *h, uint32_t H, uint32_t db) {
-    if (HK32 && H <= 32) sort_hits32_R<1>(h, H, db);
-    else if (HK32 && H <= 64) sort_hits32_R<2>(h, H, db);
-    else if (!HK32 && H <= 32) sort_hits_R<1>(h, H);
-    else if (!HK32 && H <= 64) sort_hits_R<2>(h, H);
+// Up to 64 matches are sorted in registers; the rare larger sets (<= HCAP) in shared memory.
+template <typename T>
+MT_DEV void sort_hits(T *h, uint32_t H) {
+    if (H <= 32) sort_regs<1, T>(h, H);
+    else if (H <= 64) sort_regs<2, T>(h, H);
     else {
         uint32_t P = 128;
         while (P < H) P <<= 1;
-        for (uint32_t i = H + lane_id(); i < P; i += 32) h[i] = ~0ull;
+        for (uint32_t i = H + lane_id(); i < P; i += 32) h[i] = (T)~(T)0;
         __syncwarp();
-        warp_bitonic(h, P);
+        warp_bitonic<T>(h, P);
     }
 }
 
-MT_DEV void read_kmer_at(const uint64_t *rd, uint32_t p, uint32_t k, uint32_t canonical, uint64_t &code,
-                         uint32_t &strand) {
-    uint64_t fwd, rc;
-    kmer_codes(get32(rd, p), k, fwd, rc);
-    canon(fwd, rc, canonical, code, strand);
-}
-
 template <bool SMEM_HIST, bool HK32>
-__global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
+__global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
+    using HitT = typename HitKey<HK32>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(smraw);
     const uint32_t hist_n = SMEM_HIST ? A.ix.G : 0;
-    WarpSmem *wsall = reinterpret_cast<WarpSmem *>(smraw + ((hist_n * 8 + 15) & ~15u));
+    WarpSmem<HitT> *wsall = reinterpret_cast<WarpSmem<HitT> *>(smraw + ((hist_n * 8 + 15) & ~15u));
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    WarpSmem &ws = wsall[warp];
+    WarpSmem<HitT> &ws = wsall[warp];
     if (SMEM_HIST) {
         for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x) hist[g] = 0;
         __syncthreads();
     }
     unsigned long long *H_out = SMEM_HIST ? hist : A.ghits;
     const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
+    HitKey<HK32> hf;
+    hf.db = A.ix.hk_db;
     unsigned long long n_mins = 0, n_hits = 0, n_ext = 0, n_stored = 0;
 
     const IoBlock io = *A.io;
@@ -320,31 +332,31 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             continue;
         }
         const uint32_t n = (uint32_t)n64;
-        if (warp_pack(io.reads, io.n_bases, io.vec_ok, start, n, ws.rd)) {
+        // packed read, also kept in rw for the approximation stage
+        if (warp_pack(io.reads, io.n_bases, io.vec_ok, start, n, ws.rd, A.rw + seq_word(start, io.off0, r))) {
             if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_BASE); A.qcnt[r] = 0; }
             continue;
-        }
-        {   // packed read for the approximation stage
-            uint64_t *dst = A.rw + seq_word(start, io.off0, r);
-            for (uint32_t t = lane; t < (n + 31) / 32; t += 32) dst[t] = ws.rd[t];
         }
         const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
         if (n < k || n - k + 1 < w) {
             if (lane == 0) A.qcnt[r] = 0;
             continue;
         }
-        const uint32_t nwin = n - k - w + 2;
+        const uint32_t nwin = n - k - w + 2, nk = n - k;
         uint32_t H = 0;
         bool ovf = false;
         int32_t carry = -1;
         for (uint32_t t0 = 0; t0 < nwin; t0 += TILE) {
             const uint32_t tw = min(TILE, nwin - t0);
             const uint32_t npos = tw + w - 1;
+            // codes and keys of the tile's k-mers
             for (uint32_t i = lane; i < npos; i += 32) {
-                uint64_t c;
+                uint64_t fwd, rc, code;
                 uint32_t st;
-                read_kmer_at(ws.rd, t0 + i, k, canonical, c, st);
-                ws.key[i] = mix64(c);
+                kmer_codes(get32(ws.rd, t0 + i), k, fwd, rc);
+                canon(fwd, rc, canonical, code, st);
+                ws.u.t.key[i] = mix64(code);
+                ws.u.t.code[i] = code | ((uint64_t)st << 63);
             }
             __syncwarp();
             // (w,k)-minimizers: leftmost smallest key of each window, each position once.
@@ -352,19 +364,20 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             // the k-mers [4l+3, 4l+w-1], so that minimum is found once.
             uint32_t nm = 0;
             {
+                const uint64_t *key = ws.u.t.key;
                 const uint32_t j0 = 4 * lane;
                 int32_t sel[4] = {-1, -1, -1, -1};
                 if (j0 < tw) {
                     if (w >= 4) {
                         uint32_t cp = j0 + 3;   // argmin of the shared part
-                        uint64_t ck = ws.key[cp];
+                        uint64_t ck = key[cp];
                         for (uint32_t t = j0 + 4; t < j0 + w; t++) {
-                            uint64_t kk = ws.key[t];
+                            uint64_t kk = key[t];
                             if (kk < ck) { ck = kk; cp = t; }
                         }
                         // left parts [j0+a, j0+2] (a = 0..2), right parts [j0+w, j0+a+w-1] (a = 1..3)
-                        uint64_t k0 = ws.key[j0], k1 = ws.key[j0 + 1], k2 = ws.key[j0 + 2];
-                        uint64_t r0 = ws.key[j0 + w], r1 = ws.key[j0 + w + 1], r2 = ws.key[j0 + w + 2];
+                        uint64_t k0 = key[j0], k1 = key[j0 + 1], k2 = key[j0 + 2];
+                        uint64_t r0 = key[j0 + w], r1 = key[j0 + w + 1], r2 = key[j0 + w + 2];
                         uint32_t lp2 = j0 + 2; uint64_t lk2 = k2;
                         uint32_t lp1 = (k1 <= lk2) ? j0 + 1 : lp2; uint64_t lk1 = (k1 <= lk2) ? k1 : lk2;
                         uint32_t lp0 = (k0 <= lk1) ? j0 : lp1; uint64_t lk0 = (k0 <= lk1) ? k0 : lk1;
@@ -372,25 +385,25 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
                         uint32_t rp2 = (r1 < rk1) ? j0 + w + 1 : rp1; uint64_t rk2 = (r1 < rk1) ? r1 : rk1;
                         uint32_t rp3 = (r2 < rk2) ? j0 + w + 2 : rp2; uint64_t rk3 = (r2 < rk2) ? r2 : rk2;
                         // window a = left part, shared part, right part, in position order
-                        uint32_t b0 = (lk0 <= ck) ? lp0 : cp; uint64_t bk0 = (lk0 <= ck) ? lk0 : ck;
-                        uint32_t b1 = (lk1 <= ck) ? lp1 : cp; uint64_t bk1 = (lk1 <= ck) ? lk1 : ck;
+                        const uint32_t b0 = (lk0 <= ck) ? lp0 : cp;
+                        uint32_t b1 = (lk1 <= ck) ? lp1 : cp; const uint64_t bk1 = (lk1 <= ck) ? lk1 : ck;
                         b1 = (rk1 < bk1) ? rp1 : b1;
-                        uint32_t b2 = (lk2 <= ck) ? lp2 : cp; uint64_t bk2 = (lk2 <= ck) ? lk2 : ck;
+                        uint32_t b2 = (lk2 <= ck) ? lp2 : cp; const uint64_t bk2 = (lk2 <= ck) ? lk2 : ck;
                         b2 = (rk2 < bk2) ? rp2 : b2;
-                        uint32_t b3 = (rk3 < ck) ? rp3 : cp;
-                        const uint32_t bb[4] = {b0, b1, b2, b3};
-#pragma unroll
-                        for (int a = 0; a < 4; a++)
-                            if (j0 + a < tw) sel[a] = (int32_t)(t0 + bb[a]);
+                        const uint32_t b3 = (rk3 < ck) ? rp3 : cp;
+                        sel[0] = (int32_t)(t0 + b0);
+                        if (j0 + 1 < tw) sel[1] = (int32_t)(t0 + b1);
+                        if (j0 + 2 < tw) sel[2] = (int32_t)(t0 + b2);
+                        if (j0 + 3 < tw) sel[3] = (int32_t)(t0 + b3);
                     } else {
 #pragma unroll
                         for (int a = 0; a < 4; a++) {
                             const uint32_t j = j0 + a;
                             if (j < tw) {
                                 uint32_t b = j;
-                                uint64_t bk = ws.key[j];
+                                uint64_t bk = key[j];
                                 for (uint32_t t = 1; t < w; t++) {
-                                    uint64_t kk = ws.key[j + t];
+                                    uint64_t kk = key[j + t];
                                     if (kk < bk) { bk = kk; b = j + t; }
                                 }
                                 sel[a] = (int32_t)(t0 + b);
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
                 uint32_t o = nm + incl - ne;
 #pragma unroll
                 for (int a = 0; a < 4; a++)
-                    if (em[a]) ws.mpos[o++] = (uint16_t)sel[a];
+                    if (em[a]) ws.u.t.mpos[o++] = (uint16_t)sel[a];
                 nm += __shfl_sync(FULL, incl, 31);
                 // selection of the tile's last window, for the next tile
                 const uint32_t last_lane = (tw - 1) / 4;
@@ -423,68 +436,88 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             }
             __syncwarp();
             n_mins += nm;
-            // index lookups, 32 at a time, then a cooperative gather of all their matches
+            // Index lookups, one minimizer a lane, both halves of a slot loaded together; then
+            // the round's matches are expanded across the warp.
             for (uint32_t m0 = 0; m0 < nm; m0 += 32) {
                 const uint32_t m = m0 + lane;
-                uint32_t cnt = 0;
+                uint32_t cnt = 0, ni = 0, rpos = 0, rst = 0;
+                uint64_t w1 = 0, w2 = 0, w3 = 0;
                 if (m < nm) {
-                    const uint32_t p = ws.mpos[m];
-                    uint64_t code;
-                    uint32_t st;
-                    read_kmer_at(ws.rd, p, k, canonical, code, st);
-                    const uint64_t key = ws.key[p - t0];
+                    rpos = ws.u.t.mpos[m];
+                    const uint32_t xi = rpos - t0;
+                    const uint64_t cs = ws.u.t.code[xi];
+                    const uint64_t key = ws.u.t.key[xi];
+                    rst = (uint32_t)(cs >> 63);
+                    const uint64_t want = (cs & CODE_MASK62) + 1;
                     uint64_t s = slot_of(key, A.ix.slot_shift);
-                    const uint64_t want = code + 1;
-                    uint32_t ni = 0;
-                    uint64_t w1 = 0;
                     for (uint64_t it = 0; it <= A.ix.slot_mask; it++) {
                         const ulonglong2 a = __ldg(&A.ix.table[2 * s]);
+                        const ulonglong2 b = __ldg(&A.ix.table[2 * s + 1]);
                         if (a.x == 0) break;
                         if ((a.x & CODE_MASK62) == want) {
                             ni = (uint32_t)(a.x >> 62);
-                            w1 = a.y;
+                            w1 = a.y; w2 = b.x; w3 = b.y;
                             cnt = ni ? ni : (uint32_t)(a.y >> 40);
-                            if (ni > 1) {
-                                const ulonglong2 b2 = __ldg(&A.ix.table[2 * s + 1]);
-                                ws.u.pr.inl[lane * 3 + 1] = b2.x;
-                                ws.u.pr.inl[lane * 3 + 2] = b2.y;
-                            }
                             break;
                         }
                         s = (s + 1) & A.ix.slot_mask;
                     }
                     if (cnt > A.max_occ) cnt = 0;
-                    ws.u.pr.inl[lane * 3] = w1;
-                    ws.u.pr.off[lane] = w1 & OFF_MASK40;
-                    ws.u.pr.meta[lane] = p | (st << 16) | (ni << 17);
                     if (!ni) n_ext += cnt;
                 }
                 const uint32_t incl = warp_incl_scan(cnt);
                 const uint32_t total = __shfl_sync(FULL, incl, 31);
-                ws.u.pr.pref[lane] = incl - cnt;
-                if (lane == 31) ws.u.pr.pref[32] = incl;
+                const uint32_t pre = incl - cnt;
                 if (!ovf && H + total > HCAP) {
                     // switch to counting only: count what is buffered so far
-                    for (uint32_t i = lane; i < H; i += 32) atomicAdd(&H_out[hk_genome(ws.hits[i])], 1ull);
+                    for (uint32_t i = lane; i < H; i += 32) atomicAdd(&H_out[hf.genome(ws.hits[i])], 1ull);
                     ovf = true;
                 }
-                __syncwarp();
-                const uint32_t nl = min(32u, nm - m0);
-                for (uint32_t q = lane; q < total; q += 32) {
-                    uint32_t lo = 0, hi = nl;   // owner: last lookup with pref <= q
-                    while (hi - lo > 1) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (ws.u.pr.pref[mid] <= q) lo = mid; else hi = mid;
+                if (!ovf) {
+                    // stage the lookups with matches by rank, then expand: one match a lane a
+                    // pass; a match's lookup is the last one starting at or before it
+                    const unsigned nz = __ballot_sync(FULL, cnt != 0);
+                    if (cnt) {
+                        const uint32_t c = __popc(nz & ((1u << lane) - 1u));
+                        ws.u.t.e_pre[c] = pre;
+                        ws.u.t.e_meta[c] = rpos | (rst << 16) | ((ni ? 1u : 0u) << 17);
+                        ws.u.t.e_w[3 * c] = ni ? w1 : (w1 & OFF_MASK40);
+                        if (ni) { ws.u.t.e_w[3 * c + 1] = w2; ws.u.t.e_w[3 * c + 2] = w3; }
                     }
-                    const uint32_t t = q - ws.u.pr.pref[lo];
-                    const uint32_t meta = ws.u.pr.meta[lo];
-                    const uint64_t occ = (meta >> 17) ? ws.u.pr.inl[lo * 3 + t] : __ldg(&A.ix.occ[ws.u.pr.off[lo] + t]);
-                    if (!ovf) ws.hits[H + q] = hit_key(occ, meta & 0xFFFFu, (meta >> 16) & 1u, n, k);
-                    else atomicAdd(&H_out[occ >> 33], 1ull);
+                    __syncwarp();
+                    uint32_t before = 0;    // lookups starting before this pass
+                    for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                        const uint32_t bit = (cnt && pre >= q0 && pre < q0 + 32) ? (1u << (pre - q0)) : 0u;
+                        const uint32_t M = __reduce_or_sync(FULL, bit);
+                        const uint32_t q = q0 + lane;
+                        if (q < total) {
+                            const uint32_t c = before + __popc(M & (0xFFFFFFFFu >> (31 - lane))) - 1;
+                            const uint32_t t = q - ws.u.t.e_pre[c];
+                            const uint32_t meta = ws.u.t.e_meta[c];
+                            const uint64_t occ = (meta >> 17) ? ws.u.t.e_w[3 * c + t] : __ldg(&A.ix.occ[ws.u.t.e_w[3 * c] + t]);
+                            ws.hits[H + q] = hf.make(occ, meta & 0xFFFFu, (meta >> 16) & 1u, nk);
+                        }
+                        before += __popc(M);
+                    }
+                } else {
+                    if (ni && cnt) {
+#pragma unroll
+                        for (uint32_t t = 0; t < 3; t++)
+                            if (t < cnt) atomicAdd(&H_out[(t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33], 1ull);
+                    }
+                    unsigned ext = __ballot_sync(FULL, ni == 0 && cnt != 0);
+                    while (ext) {
+                        const int src = __ffs(ext) - 1;
+                        ext &= ext - 1;
+                        const uint32_t c = __shfl_sync(FULL, cnt, src);
+                        const uint64_t off = __shfl_sync(FULL, w1 & OFF_MASK40, src);
+                        for (uint32_t q = lane; q < c; q += 32) atomicAdd(&H_out[__ldg(&A.ix.occ[off + q]) >> 33], 1ull);
+                    }
                 }
-                H += total;
                 __syncwarp();
+                H += total;
             }
+            __syncwarp();
         }
         n_hits += H;
         if (ovf) {
@@ -499,12 +532,12 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
             if (lane == 0) A.qcnt[r] = 0;
             continue;
         }
-        sort_hits<HK32>(ws.hits, H, A.ix.hk_db);
+        sort_hits<HitT>(ws.hits, H);
         // (genome, strand) groups of the sorted matches, in order
         uint32_t ng = 0;
         for (uint32_t i0 = 0; i0 < H; i0 += 32) {
             const uint32_t i = i0 + lane;
-            const bool st = i < H && (i == 0 || (ws.hits[i] >> 33) != (ws.hits[i - 1] >> 33));
+            const bool st = i < H && (i == 0 || hf.grel(ws.hits[i]) != hf.grel(ws.hits[i - 1]));
             const unsigned bal = __ballot_sync(FULL, st);
             if (st) ws.u.wk.gs[ng + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)i;
             ng += __popc(bal);
@@ -516,12 +549,12 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
         for (uint32_t gi = lane; gi < ng; gi += 32) {
             uint32_t s = ws.u.wk.gs[gi];
             const uint32_t ge = ws.u.wk.gs[gi + 1];
-            atomicAdd(&H_out[hk_genome(ws.hits[s])], (unsigned long long)(ge - s));
+            atomicAdd(&H_out[hf.genome(ws.hits[s])], (unsigned long long)(ge - s));
             while (s < ge) {
-                const uint32_t e = lower_bound_u64(ws.hits, s + 1, ge, ws.hits[s] + E + 1);
+                const uint32_t e = lower_bound_t<HitT>(ws.hits, s + 1, ge, (HitT)(ws.hits[s] + E + 1));
                 if (e - s >= A.min_seeds) {
                     const uint32_t qi = atomicAdd(&ws.u.wk.qcount, 1u);
-                    ws.u.wk.qs[qi] = (uint16_t)s;
+                    ws.u.wk.qk[qi] = ws.hits[s];
                     ws.u.wk.qn[qi] = (uint16_t)(e - s);
                 }
                 s = e;
@@ -532,16 +565,16 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed(SeedArgs A) {
         // rank the qualifying locations: seeds descending, then (genome, strand, diagonal)
         for (uint32_t qi = lane; qi < Q; qi += 32) {
             const uint32_t seeds_i = ws.u.wk.qn[qi];
-            const uint64_t hk_i = ws.hits[ws.u.wk.qs[qi]];
+            const HitT hk_i = ws.u.wk.qk[qi];
             uint32_t rank = 0;
             for (uint32_t qj = 0; qj < Q; qj++) {
                 const uint32_t seeds_j = ws.u.wk.qn[qj];
-                const uint64_t hk_j = ws.hits[ws.u.wk.qs[qj]];
+                const HitT hk_j = ws.u.wk.qk[qj];
                 rank += (seeds_j > seeds_i) || (seeds_j == seeds_i && hk_j < hk_i);
             }
             if (rank < CSTORE) {
                 Cluster c;
-                c.hkey = hk_i; c.seeds = seeds_i; c.pad = 0;
+                c.hkey = hf.wide(hk_i); c.seeds = seeds_i; c.pad = 0;
                 A.clus[r * CSTORE + rank] = c;
             }
         }
@@ -1074,7 +1107,7 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         A.ctr = ctr;
         const bool smem_hist = G <= SMEM_HIST_MAX;
         const bool hk32 = ix->hk_db != 0;
-        const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem);
+        const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * (hk32 ? sizeof(WarpSmem<uint32_t>) : sizeof(WarpSmem<uint64_t>));
         const uint64_t need = (c.cap_reads + SEED_WARPS - 1) / SEED_WARPS;
         int rc = hk32 ? (smem_hist ? launch_seed<true, true>(A, smem, need, s) : launch_seed<false, true>(A, smem, need, s))
                       : (smem_hist ? launch_seed<true, false>(A, smem, need, s) : launch_seed<false, false>(A, smem, need, s));

@@ -60,6 +60,24 @@ def test_tiny_workload_device_buffers(mt, tiny):
     compare_classify(out, ref)
 
 
+@pytest.mark.parametrize("shift", [0, 3])
+def test_device_reads_mid_buffer(mt, tiny, shift):
+    """A batch whose first read starts inside the device buffer, with the buffer at an aligned
+    address (vector loads and prefetch) and at an odd one (byte loads)."""
+    import torch
+    c, g, r, ix, oix = tiny
+    prm = _params(c)
+    a, b = 1234, 5679
+    seq = r.seq[int(r.offsets[a]):int(r.offsets[b])]
+    ref = oracle.classify(oix, seq, r.offsets[a:b + 1] - r.offsets[a], oracle_params(prm))
+    buf = torch.zeros(len(r.seq) + 16, dtype=torch.uint8, device="cuda")
+    view = buf[shift:shift + len(r.seq)]
+    view.copy_(torch.from_numpy(r.seq))
+    assert (view.data_ptr() % 16 == 0) == (shift == 0)
+    out = mt.classify(ix, view, torch.from_numpy(r.offsets[a:b + 1].astype(np.int64)).cuda(), **prm)
+    compare_classify(out, ref)
+
+
 def test_index_counts_match_oracle(mt, tiny):
     c, g, r, ix, oix = tiny
     info = ix.info()
