@@ -34,7 +34,7 @@ METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact)
 # kernel on 2e6 reads of the same workload (dram__bytes_read.sum + dram__bytes_write.sum); the
 # index is fixed, so traffic grows in proportion to the reads. None whenever the kernel has
 # changed since the last capture.
-SEED_DRAM_BYTES_PER_READ = None
+SEED_DRAM_BYTES_PER_READ = (7.318767e9 + 0.250638e9) / 2e6
 WORKLOAD = ("medium: 200 genomes x 2 Mb (20 clades x 10, 1-10% divergence), k21 w11 canonical, "
             "1e7 reads x 150 bp (both strands, 0.5% subst + 0.05% indel, 5% random), E=8, min_seeds 3, top 3")
 
@@ -153,6 +153,31 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
+def gather_ceiling(torch, n_idx=1 << 26, table_gib=4, reps=5):
+    """Random-access ceiling of this GPU: 8-byte words gathered at uniformly random indices
+    from a table far larger than L2 by the library gather (torch.index_select). The index
+    reads and output writes are streaming and inside the timed region, so the rate is a
+    slight underestimate. Returns G gathers/s."""
+    table = torch.ones(table_gib << 27, dtype=torch.int64, device="cuda")
+    gen_ = torch.Generator(device="cuda")
+    gen_.manual_seed(99)
+    idx = torch.randint(0, table.numel(), (n_idx,), device="cuda", generator=gen_)
+    out = torch.empty(n_idx, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        torch.index_select(table, 0, idx, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        torch.index_select(table, 0, idx, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del table, idx, out
+    torch.cuda.empty_cache()
+    return n_idx / (ms / 1000.0) / 1e9
+
+
 def timed_steps(fn, steps, warmup, stream, torch):
     for _ in range(warmup):
         fn()
@@ -374,12 +399,21 @@ def run_ours(args):
                   + st["n_ext_occ"] * 8             # occurrences outside the slot
                   + n_reads * 4 + st["n_stored"] * 16)   # location counts and records out
     hbm, peak_kind = peaks()
+    seed_requests = st["n_minimizers"] + st["n_ext_occ"] * 8 / 32.0
+    gather_gps = gather_ceiling(torch)
     achieved = seed_bytes / (st["ms_seed"] / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (SEED_DRAM_BYTES_PER_READ * n_reads if SEED_DRAM_BYTES_PER_READ else None),
                 "kernel": "k_seed",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": seed_bytes, "ms_per_launch": st["ms_seed"],
+                "random_access": {"achieved": seed_requests / (st["ms_seed"] / 1000.0) / 1e9,
+                                  "peak": gather_gps, "unit": "G random requests/s",
+                                  "frac": seed_requests / (st["ms_seed"] / 1000.0) / 1e9 / gather_gps,
+                                  "requests_per_launch": seed_requests,
+                                  "requests": "one 32-byte slot per lookup + occurrence-list bytes / 32",
+                                  "peak_kind": "measured in this run: torch.index_select of 8-byte words at "
+                                               "2^26 random indices over a 4 GiB table"},
                 "stage_ms": {k[3:]: st[k] for k in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")}}
 
     line = {"metric": METRIC, "value": value, "unit": "reads/s", "n_gpus": world, "steps": args.steps,
