@@ -5,8 +5,8 @@
 // equals window base E + j + d. From column c the walk follows the longest zero run of any
 // row, counts the obstacle that ends it and steps over it; more than E obstacles rejects.
 //
-// Bit-parallel form: a group of G lanes works on one pair. Each lane owns the diagonals
-// di = lane, lane + G, ... (di = E + d is the window offset of the row). The run of a row
+// Bit-parallel form: a group of G lanes works on one pair. Each lane owns a contiguous range
+// of ceil((2E+1)/G) diagonals (di = E + d is the window offset of the row). The run of a row
 // from column c ends at its next mismatch, found 32 columns at a time by XOR-ing 64-bit
 // slices of the 2-bit packed read and window, folding each 2-bit group to one bit and
 // taking the lowest set bit. The group then takes the furthest run end with one
