@@ -48,6 +48,23 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (for times: the slowest rank); x itself on one rank.
+    Every rank must call it, in the same order."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -343,17 +360,13 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_reads / (ms / 1000.0)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    value = job_rate(n_reads, world, ms)
     batched_out = out
 
     # plain form on the same inputs: identical outputs required
     ms_plain, outs = timed_steps(step(mt.MT_EDA_PLAIN), args.steps, 1, stream, torch)
+    ms_plain = max_over_ranks(ms_plain, world)
     plain_out = outs[-1]
     identical = (torch.equal(batched_out["taxon"], plain_out["taxon"])
                  and torch.equal(batched_out["locs"], plain_out["locs"])
@@ -364,6 +377,7 @@ def run_ours(args):
     plan = mt.Plan(ix, max_reads=n_reads, max_bases=n_bases, max_read_len=int(reads.lengths.max()),
                    **params(c, mt.MT_EDA_BATCHED))
     ms_graph, gouts = timed_steps(lambda: plan.classify(d_reads, d_off), args.steps, 3, stream, torch)
+    ms_graph = max_over_ranks(ms_graph, world)
     graph_out = gouts[-1]
     graph_identical = (torch.equal(batched_out["taxon"], graph_out["taxon"])
                        and torch.equal(batched_out["locs"], graph_out["locs"])
@@ -388,6 +402,8 @@ def run_ours(args):
     e2e_graph_ms, _ = timed_steps(lambda: plan.classify(h_reads.numpy(), h_off.numpy().view(np.uint64), out=h_out),
                                   max(1, args.steps // 2), 1, stream, torch)
     plan.close()
+    e2e_ms = max_over_ranks(e2e_ms, world)
+    e2e_graph_ms = max_over_ranks(e2e_graph_ms, world)
     h2d = n_bases + (n_reads + 1) * 8
     d2h = n_reads * (4 + 1 + 24 * top_n) + G * 16
 
@@ -424,12 +440,12 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (%.2f GB reads, %.2f GB index)" % (n_bases / 1e9, info["device_bytes"] / 1e9)},
             "pairs_per_s": st["n_candidates"] / (ms / 1000.0) * world,
-            "plain": {"value": world * n_reads / (ms_plain / 1000.0), "ms_per_step": ms_plain, "identical": identical},
-            "graph": {"value": world * n_reads / (ms_graph / 1000.0), "ms_per_step": ms_graph,
+            "plain": {"value": job_rate(n_reads, world, ms_plain), "ms_per_step": ms_plain, "identical": identical},
+            "graph": {"value": job_rate(n_reads, world, ms_graph), "ms_per_step": ms_graph,
                       "identical": graph_identical,
-                      "e2e_value": world * n_reads / (e2e_graph_ms / 1000.0), "e2e_ms_per_step": e2e_graph_ms},
+                      "e2e_value": job_rate(n_reads, world, e2e_graph_ms), "e2e_ms_per_step": e2e_graph_ms},
             "roofline": roofline,
-            "e2e": {"value": world * n_reads / (e2e_ms / 1000.0), "unit": "reads/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(n_reads, world, e2e_ms), "unit": "reads/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "clocks": clocks, "gpu_launches": int(st["n_launches"]) * args.steps,
             "index": {"build_s": index_s, **info},

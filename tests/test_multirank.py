@@ -1,0 +1,90 @@
+"""Multi-rank host logic of bench.py on CPU: two gloo ranks (world size 2, 127.0.0.1).
+
+The path shards as independent batches, one per rank (replicas, weak scaling): no collective
+sits on the data path. What runs across ranks is the timing contract: every rank reports its
+own time, the job's time is the slowest rank's, and the job's throughput counts the units of
+all ranks; only rank 0 prints, and the reference arm does no work on other ranks."""
+import json
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(RANK=str(rank), LOCAL_RANK=str(rank), WORLD_SIZE=str(world),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, local, w = bench.dist_env()
+    my_ms = 10.0 + 5.0 * rank                   # rank 1 is the slow one
+    ms = bench.max_over_ranks(my_ms, w, device="cpu")
+    second = bench.max_over_ranks(100.0 - rank, w, device="cpu")   # a second reduction, same order
+    rate = bench.job_rate(1000, w, ms)
+    printed = None
+    if rank != 0:
+        # the reference arm returns at once on ranks other than 0 (no data, no output)
+        import contextlib
+        import io
+        buf = io.StringIO()
+        with contextlib.redirect_stdout(buf):
+            bench.run_reference(type("A", (), dict(steps=1, warmup=3, ref_sample=10))())
+        printed = buf.getvalue()
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, "rank%d.json" % rank), "w") as f:
+        json.dump(dict(env=[r, local, w], ms=ms, second=second, rate=rate, printed=printed), f)
+
+
+def test_two_gloo_ranks_take_the_slowest_time(tmp_path):
+    import torch.multiprocessing as tmp
+    port = _free_port()
+    tmp.spawn(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    res = [json.load(open(tmp_path / ("rank%d.json" % r))) for r in range(2)]
+    for r, x in enumerate(res):
+        assert x["env"] == [r, r, 2]
+        assert x["ms"] == 15.0                   # the slowest rank's time on every rank
+        assert x["second"] == 100.0
+        assert x["rate"] == pytest.approx(2 * 1000 / 0.015)
+    assert res[1]["printed"] == ""
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    assert bench.job_rate(10_000_000, 1, 31.6) == pytest.approx(1e7 / 0.0316)
+
+
+def test_clock_samples_are_parsed_without_a_gpu(tmp_path):
+    """The nvidia-smi sample parser: median SM clock, max clock, active throttle reasons."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1995, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbled line"]
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+
+    class Done:
+        def terminate(self): pass
+        def wait(self, timeout=None): return 0
+    c.p = Done()
+    c.f = open(os.devnull, "w")
+    out = c.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
