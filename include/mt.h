@@ -37,6 +37,7 @@ extern "C" {
 #define MT_ECUDA (-4)       /* a CUDA runtime error (see mt_last_cuda_error) */
 #define MT_ECANCELED (-5)   /* a serving request was cancelled */
 #define MT_EBUSY (-6)       /* a serving request is still in flight */
+#define MT_EXCHANGE (-7)    /* the caller's allreduce of a sharded batch failed */
 
 /* ---- limits ---------------------------------------------------------------------------- */
 #define MT_MAX_READ_LEN 1024u   /* bases per read (the paper targets short reads) */
@@ -165,6 +166,37 @@ int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
                 const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
                 int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
                 uint64_t *genome_hits, double *abundance, mt_stats *stats);
+
+/* ---- one batch sharded over several processes (ranks) -------------------------------------
+ * Stages 1 and 3 are defined over the whole batch: the containment cutoff compares a genome's
+ * hits with the largest hit count of the batch ("The MetaTrinity Pipeline", stage 1), and a
+ * multi-mapped read is split by the batch's unique counts (Fig. 1, 3a-b). A batch cut into
+ * shards, one per rank, therefore needs three element-wise sums over the ranks, which the
+ * caller supplies as `allreduce`. The call runs the stages of its own shard and, at each
+ * exchange point, copies a vector of n_genomes values to a host buffer and calls
+ * allreduce(ctx, kind, buf, n_genomes); that must replace buf with the element-wise sum of
+ * every rank's buf (all ranks make the same exchanges in the same order) and return 0:
+ *   MT_XCHG_GENOME_HITS (uint64): seed hits per genome, before the containment cutoff;
+ *   MT_XCHG_UNIQUE (uint64): uniquely mapped reads per genome, before the multi-mapped split;
+ *   MT_XCHG_MULTI (double): multi-mapped read shares per genome, before the abundances.
+ * Each rank then reports for its own reads exactly what mt_classify reports for them in the
+ * whole batch; genome_hits and abundance are the whole batch's on every rank (abundance up to
+ * the order in which doubles are summed). A rank with no reads still makes the call and
+ * contributes zeros. Arguments are those of mt_classify plus allreduce (not NULL) and ctx
+ * (passed through). The calls of one rank run on its own stream; the exchanges block the
+ * calling host thread only.
+ * Errors: those of mt_classify; a call that fails its argument checks returns before its first
+ * exchange (the other ranks' allreduce must then fail on its own, e.g. by a time limit);
+ * MT_EXCHANGE when allreduce returns non-zero (the call stops at that exchange). */
+#define MT_XCHG_GENOME_HITS 0
+#define MT_XCHG_UNIQUE 1
+#define MT_XCHG_MULTI 2
+typedef int (*mt_allreduce_fn)(void *ctx, int kind, void *buf, uint64_t count);
+int mt_classify_sharded(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
+                        const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
+                        int device_ptrs, void *stream, mt_allreduce_fn allreduce, void *ctx,
+                        int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits,
+                        double *abundance, mt_stats *stats);
 
 /* ---- batched form with a captured CUDA graph ---------------------------------------------
  * A plan holds a preallocated workspace sized for batches of up to max_reads reads,

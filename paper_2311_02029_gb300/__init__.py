@@ -20,6 +20,10 @@ LIB_PATH = os.path.join(_HERE, "libmt.so")
 _lib = None
 
 MT_OK, MT_EINVAL, MT_ENOMEM, MT_ETIMEDOUT, MT_ECUDA, MT_ECANCELED, MT_EBUSY = 0, -1, -2, -3, -4, -5, -6
+MT_EXCHANGE = -7
+MT_XCHG_GENOME_HITS, MT_XCHG_UNIQUE, MT_XCHG_MULTI = 0, 1, 2
+# mt_allreduce_fn: int (*)(void *ctx, int kind, void *buf, uint64_t count)
+AllreduceFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64)
 MT_EDA_BATCHED, MT_EDA_PLAIN = 0, 1
 MAX_READ_LEN, MAX_E, MAX_TOPN = 1024, 127, 8
 
@@ -70,7 +74,7 @@ class IndexInfo(ctypes.Structure):
 
 
 EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
-           "mt_index_get_info", "mt_classify", "mt_classify_workspace_bytes", "mt_pack_seqs",
+           "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
            "mt_server_cancel", "mt_server_destroy"]
@@ -97,6 +101,9 @@ def lib():
         L.mt_classify.restype = i32
         L.mt_classify.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
                                   vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.mt_classify_sharded.restype = i32
+        L.mt_classify_sharded.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
+                                          AllreduceFn, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.mt_classify_workspace_bytes.restype = u64
         L.mt_classify_workspace_bytes.argtypes = [vp, u64, u64, u32, ctypes.POINTER(ClassifyParams)]
         L.mt_pack_seqs.restype = i32
@@ -218,13 +225,22 @@ def classify_params(e_abs=0, e_permille=100, min_seeds=3, top_n=3, max_occ=1024,
                           abund_cutoff)
 
 
-def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None, **params) -> dict:
-    """``mt_classify`` over one read batch. ``reads``/``offsets`` are either host arrays
-    (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors).
-    ``out`` may hold preallocated host output arrays (e.g. in pinned memory)."""
+def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params) -> dict:
+    """Marshalling shared by ``classify`` and ``classify_sharded`` (cb: an AllreduceFn or None)."""
     p = classify_params(**params)
     st = Stats()
     G = ix.n_genomes
+
+    def call(rptr, nb, optr, n_reads, dev):
+        L = lib()
+        if cb is None:
+            return L.mt_classify(ix.handle, rptr, nb, optr, n_reads, ctypes.byref(p), dev, _stream(stream),
+                                 _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                 _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+        return L.mt_classify_sharded(ix.handle, rptr, nb, optr, n_reads, ctypes.byref(p), dev, _stream(stream),
+                                     cb, None, _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                     _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+
     if _is_torch(reads) and reads.is_cuda:
         import torch
         dev = reads.device
@@ -234,9 +250,7 @@ def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None
                    locs=torch.empty((n_reads, p.top_n, 24), dtype=torch.uint8, device=dev) if want_locs else None,
                    genome_hits=torch.empty(G, dtype=torch.int64, device=dev),
                    abundance=torch.empty(G, dtype=torch.float64, device=dev))
-        rc = lib().mt_classify(ix.handle, _ptr(reads), reads.numel(), _ptr(offsets), n_reads, ctypes.byref(p), 1,
-                               _stream(stream), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
-                               _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
+        rc = call(_ptr(reads), reads.numel(), _ptr(offsets), n_reads, 1)
     else:
         r = _host_u8(reads)
         off = _host_u64(offsets)
@@ -247,12 +261,59 @@ def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None
                        genome_hits=np.empty(G, np.uint64), abundance=np.empty(G, np.float64))
         else:
             out = dict(out)
-        rc = lib().mt_classify(ix.handle, _ptr(r), len(r), _ptr(off), n_reads, ctypes.byref(p), 0,
-                               _stream(stream), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
-                               _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
-    _check(rc, "mt_classify")
+        rc = call(_ptr(r), len(r), _ptr(off), n_reads, 0)
+    _check(rc, "mt_classify" if cb is None else "mt_classify_sharded")
     out["stats"] = st.as_dict()
     return out
+
+
+def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None, **params) -> dict:
+    """``mt_classify`` over one read batch. ``reads``/``offsets`` are either host arrays
+    (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors).
+    ``out`` may hold preallocated host output arrays (e.g. in pinned memory)."""
+    return _classify(ix, reads, offsets, None, stream, want_locs, out, params)
+
+
+def allreduce_callback(fn) -> AllreduceFn:
+    """Wraps ``fn(kind, buf)`` as an ``mt_allreduce_fn``: buf is a numpy view of the exchanged
+    vector (uint64 for MT_XCHG_GENOME_HITS and MT_XCHG_UNIQUE, float64 for MT_XCHG_MULTI) that
+    fn must replace in place with its element-wise sum over the ranks. An exception in fn is
+    reported to the library as a failed exchange. Keep the returned object alive for the call."""
+    def tramp(ctx, kind, buf, count):
+        try:
+            ctype = ctypes.c_double if kind == MT_XCHG_MULTI else ctypes.c_uint64
+            arr = np.ctypeslib.as_array((ctype * max(int(count), 1)).from_address(buf))[:int(count)]
+            fn(int(kind), arr)
+            return 0
+        except Exception:
+            return 1
+    return AllreduceFn(tramp)
+
+
+def dist_allreduce(group=None):
+    """An exchange function for ``allreduce_callback`` over a torch.distributed process group
+    (gloo: host tensors; nccl: the current CUDA device)."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(kind, arr):
+        t = torch.from_numpy(arr.view(np.int64) if arr.dtype == np.uint64 else arr)
+        if dist.get_backend(group) == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        res = t.cpu().numpy()
+        arr[...] = res.view(arr.dtype) if arr.dtype == np.uint64 else res
+    return fn
+
+
+def classify_sharded(ix: Index, reads, offsets, allreduce, *, stream=None, want_locs=True, out=None,
+                     **params) -> dict:
+    """``mt_classify_sharded``: this rank's shard of one batch; ``allreduce(kind, buf)`` sums a
+    vector over the ranks in place (see ``dist_allreduce``). Per-read results are those of
+    ``classify`` on the whole batch for this rank's reads; genome_hits and abundance are the
+    whole batch's."""
+    cb = allreduce_callback(allreduce)
+    return _classify(ix, reads, offsets, cb, stream, want_locs, out, params)
 
 
 class Plan:

@@ -1062,7 +1062,22 @@ struct EnqueueCtx {
     bool allow_tune;
     cudaEvent_t *ev;       // 5 events or null
     uint64_t launches;
+    mt_allreduce_fn xfn;   // sum over the ranks of a sharded batch, or null
+    void *xctx;
 };
+
+// Replaces the G-vector at `dev` with its sum over the ranks of a sharded batch (a no-op for an
+// unsharded call): device -> host, the caller's allreduce, host -> device.
+static int exchange(const EnqueueCtx &c, cudaStream_t s, void *dev, uint32_t G, int kind) {
+    if (!c.xfn) return MT_OK;
+    std::vector<uint64_t> h(std::max<uint32_t>(G, 1u), 0);
+    if (G) MT_CK(cudaMemcpyAsync(h.data(), dev, G * 8ull, cudaMemcpyDeviceToHost, s));
+    MT_CK(cudaStreamSynchronize(s));
+    if (c.xfn(c.xctx, kind, h.data(), G) != 0) return MT_EXCHANGE;
+    if (G) MT_CK(cudaMemcpyAsync(dev, h.data(), G * 8ull, cudaMemcpyHostToDevice, s));
+    MT_CK(cudaStreamSynchronize(s));
+    return MT_OK;
+}
 
 template <bool SH, bool HK32>
 static int launch_seed(const SeedArgs &A, size_t smem, uint64_t need, cudaStream_t s) {
@@ -1113,6 +1128,7 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
                       : (smem_hist ? launch_seed<true, false>(A, smem, need, s) : launch_seed<false, false>(A, smem, need, s));
         if (rc) return rc;
         mark(1);
+        if ((rc = exchange(c, s, ghits, G, MT_XCHG_GENOME_HITS))) return rc;
 
         k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
         MT_CK(cudaGetLastError());
@@ -1156,11 +1172,17 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         D.ctr = ctr;
         k_decide<<<rblocks, 256, 0, s>>>(D);
         MT_CK(cudaGetLastError());
+        if ((rc = exchange(c, s, U, G, MT_XCHG_UNIQUE))) return rc;
         k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(D.multi_list, ctr, D.multi_set, top_n, U, M);
         MT_CK(cudaGetLastError());
+        if ((rc = exchange(c, s, M, G, MT_XCHG_MULTI))) return rc;
         c.launches += 7;   // seed, mask, select, fallback, approximation, decide, multi
     } else {
         mark(1); mark(2); mark(3);
+        int rc;   // an empty shard still takes part in every exchange, with zeros
+        if ((rc = exchange(c, s, ghits, G, MT_XCHG_GENOME_HITS))) return rc;
+        if ((rc = exchange(c, s, U, G, MT_XCHG_UNIQUE))) return rc;
+        if ((rc = exchange(c, s, M, G, MT_XCHG_MULTI))) return rc;
     }
     k_abund<<<1, 1024, 0, s>>>(G, U, M, p->abund_cutoff, (double *)P(L.abund));
     MT_CK(cudaGetLastError());
@@ -1217,10 +1239,10 @@ extern "C" uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_b
     return plan_layout(ix, n_bases, n_reads, p->top_n, std::max<uint32_t>(maxn, 1), p->max_occ, true).total;
 }
 
-extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
-                           uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
-                           int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
-                           mt_stats *stats) {
+static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                         uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
+                         mt_allreduce_fn xfn, void *xctx, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                         uint64_t *genome_hits, double *abundance, mt_stats *stats) {
     if (!ix || !offsets || (!taxon && n_reads) || (!reads && n_bases)) return MT_EINVAL;
     int rc = check_params(p);
     if (rc) return rc;
@@ -1288,7 +1310,8 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     if (stats)
         for (auto &e : ev) MT_CK(cudaEventCreate(&e));
-    EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, true, stats ? ev : nullptr, launches};
+    EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, true, stats ? ev : nullptr, launches,
+                   xfn, xctx};
     rc = enqueue_classify(ctx, s);
     if (rc) { dfree(ws, s); return rc; }
 
@@ -1308,6 +1331,24 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
     if (stats)
         for (auto &e : ev) cudaEventDestroy(e);
     return status_of(h.err);
+}
+
+extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                           uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
+                           int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
+                           mt_stats *stats) {
+    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, nullptr, nullptr, taxon, nloc,
+                         locs, genome_hits, abundance, stats);
+}
+
+extern "C" int mt_classify_sharded(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
+                                   const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *p,
+                                   int device_ptrs, void *stream, mt_allreduce_fn allreduce, void *ctx,
+                                   int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits,
+                                   double *abundance, mt_stats *stats) {
+    if (!allreduce) return MT_EINVAL;
+    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, allreduce, ctx, taxon, nloc,
+                         locs, genome_hits, abundance, stats);
 }
 
 // ---- plans: preallocated workspace + captured CUDA graph ---------------------------------------------

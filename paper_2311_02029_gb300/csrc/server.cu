@@ -267,6 +267,7 @@ extern "C" const char *mt_strerror(int status) {
         case MT_ECUDA: return "CUDA runtime error";
         case MT_ECANCELED: return "cancelled";
         case MT_EBUSY: return "still in flight";
+        case MT_EXCHANGE: return "the allreduce of a sharded batch failed";
         default: return "unknown status";
     }
 }

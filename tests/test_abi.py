@@ -64,6 +64,10 @@ def test_status_strings_and_argument_checks_without_gpu(mtlib):
                             ctypes.byref(p), None, ctypes.byref(out)) == mtlib.MT_EINVAL
     assert L.mt_eda_batch(None, None, 0, None, None, None, None, 5, 7, None, None) == mtlib.MT_EINVAL
     assert L.mt_server_create(None, 1, 1, None, ctypes.byref(out)) == mtlib.MT_EINVAL
+    cp = mtlib.classify_params()
+    assert L.mt_classify_sharded(None, None, 0, None, 0, ctypes.byref(cp), 0, None, mtlib.AllreduceFn(), None,
+                                 None, None, None, None, None, None) == mtlib.MT_EINVAL   # no allreduce
+    assert L.mt_strerror(mtlib.MT_EXCHANGE) != L.mt_strerror(-99)
 
 
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):

@@ -88,3 +88,47 @@ def test_clock_samples_are_parsed_without_a_gpu(tmp_path):
     out = c.stop()
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]
+
+
+def _xchg_main(rank, world, port, out_dir):
+    """One rank of the sharded-batch exchange: the library's callback type wrapping the
+    torch.distributed allreduce, called through its C function pointer as the library does."""
+    import ctypes
+
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import paper_2311_02029_gb300 as mt
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    cb = mt.allreduce_callback(mt.dist_allreduce())
+    fnptr = ctypes.cast(cb, ctypes.c_void_p).value
+    call = mt.AllreduceFn(fnptr)
+    hits = np.array([5, 0, 2 ** 40 + rank, 7 * rank], np.uint64)
+    uniq = np.array([rank, 1, 0, 3], np.uint64)
+    multi = np.array([0.25 * (rank + 1), 1e-17, 0.0, 2.5], np.float64)
+    rcs = [call(None, mt.MT_XCHG_GENOME_HITS, hits.ctypes.data, len(hits)),
+           call(None, mt.MT_XCHG_UNIQUE, uniq.ctypes.data, len(uniq)),
+           call(None, mt.MT_XCHG_MULTI, multi.ctypes.data, len(multi))]
+    empty = np.zeros(1, np.uint64)   # an index with no genomes still exchanges (count 0)
+    rcs.append(call(None, mt.MT_XCHG_GENOME_HITS, empty.ctypes.data, 0))
+
+    def broken(kind, arr):
+        raise RuntimeError("peer lost")
+    rcs.append(mt.allreduce_callback(broken)(None, mt.MT_XCHG_UNIQUE, uniq.ctypes.data, len(uniq)))
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, "x%d.json" % rank), "w") as f:
+        json.dump(dict(rcs=rcs, hits=[int(x) for x in hits], uniq=[int(x) for x in uniq],
+                       multi=[float(x) for x in multi]), f)
+
+
+def test_sharded_exchange_sums_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as tmp
+    tmp.spawn(_xchg_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    res = [json.load(open(tmp_path / ("x%d.json" % r))) for r in range(2)]
+    for x in res:
+        assert x["rcs"] == [0, 0, 0, 0, 1]
+        assert x["hits"] == [10, 0, 2 ** 41 + 1, 7]
+        assert x["uniq"] == [1, 2, 0, 6]
+        assert x["multi"] == [0.75, 2e-17, 0.0, 5.0]
