@@ -73,9 +73,16 @@ def _L():
         lib.or_eda_ascii.restype = u32
         lib.or_eda_ascii.argtypes = [vp, u32, vp, u32]
         lib.or_eda_batch.restype = ctypes.c_int
-        lib.or_eda_batch.argtypes = [vp, vp, vp, vp, vp, vp, u64, vp]
+        lib.or_eda_batch.argtypes = [vp, vp, vp, vp, vp, vp, u64, u32, vp]
+        for fn in ("or_hd_codes", "or_bc_codes", "or_qgram_codes", "or_shd_codes"):
+            getattr(lib, fn).restype = u32
+            getattr(lib, fn).argtypes = [vp, u32, vp, u32]
+        lib.or_qgram_q.restype = u32
+        lib.or_qgram_q.argtypes = [vp, u32, vp, u32, u32]
+        lib.or_approx_codes.restype = u32
+        lib.or_approx_codes.argtypes = [u32, vp, u32, vp, u32]
         lib.or_map_reads.restype = ctypes.c_int
-        lib.or_map_reads.argtypes = [vp, vp, vp, u64, u32, u32, u32, u32, u32, vp, vp, vp, vp,
+        lib.or_map_reads.argtypes = [vp, vp, vp, u64, u32, u32, u32, u32, u32, u32, vp, vp, vp, vp,
                                      vp, vp]
         lib.or_abundance.argtypes = [vp, u32, vp, u64, u32, ctypes.c_double, vp]
         _lib = lib
@@ -156,8 +163,10 @@ class Index:
         return (out >> np.uint64(33)).astype(np.int64), ((out >> np.uint64(1)) & np.uint64(0xFFFFFFFF)).astype(np.int64), (out & np.uint64(1)).astype(np.uint8)
 
 
+# eda_algo: 0 SneakySnake, 1 Hamming distance, 2 Base Counting, 3 q-gram (q = 5), 4 SHD
 DEFAULT_PARAMS = dict(max_occ=1024, e_abs=0, e_permille=100, min_seeds=3, top_n=3,
-                      cont_num=1, cont_den=10000, abund_cutoff=1e-4)
+                      cont_num=1, cont_den=10000, abund_cutoff=1e-4, eda_algo=0)
+ALGOS = {"sneakysnake": 0, "hamming": 1, "base_counting": 2, "qgram": 3, "shd": 4}
 
 
 def params(**kw) -> dict:
@@ -196,7 +205,7 @@ def map_reads(ix: Index, reads_seq, reads_off, p: dict, keep: np.ndarray):
     U = np.zeros(ix.G, np.uint64)
     keep = np.ascontiguousarray(keep, dtype=np.uint8)
     rc = _L().or_map_reads(ix._h, _p(s), _p(off), n, p["max_occ"], p["e_abs"], p["e_permille"],
-                           p["min_seeds"], tn, _p(keep), _p(taxon), _p(locs), _p(nloc),
+                           p["min_seeds"], tn, p.get("eda_algo", 0), _p(keep), _p(taxon), _p(locs), _p(nloc),
                            _p(multi), _p(U))
     if rc != 0:
         raise OracleError("or_map_reads failed: %d" % rc)
@@ -290,9 +299,7 @@ for _i, _b in enumerate(b"ACGT"):
     _CODE[_b] = _i
 
 
-def eda(read, window, E: int, obstacles=None) -> int:
-    """SneakySnake approximation of one pair. ``window`` has len(read) + 2E bases;
-    ``obstacles`` (bool array over the window) marks bases outside the genome."""
+def _codes_pair(read, window, E: int, obstacles=None):
     r = _CODE[_u8(read)]
     W = _CODE[_u8(window)].copy()
     if (r == 255).any() or (W == 255).any():
@@ -301,14 +308,31 @@ def eda(read, window, E: int, obstacles=None) -> int:
         raise OracleError("window length must be read length + 2E")
     if obstacles is not None:
         W[np.asarray(obstacles, dtype=bool)] = 4
-    r = np.ascontiguousarray(r)
-    W = np.ascontiguousarray(W)
+    return np.ascontiguousarray(r), np.ascontiguousarray(W)
+
+
+def approx(read, window, E: int, algo: int = 0, obstacles=None) -> int:
+    """Approximation ``algo`` (see ALGOS) of one pair, as ``eda``."""
+    r, W = _codes_pair(read, window, E, obstacles)
+    return int(_L().or_approx_codes(algo, _p(r), len(r), _p(W), E))
+
+
+def qgram_q(read, window, E: int, q: int, obstacles=None) -> int:
+    """The q-gram estimate for any q in [1, 8] (the pipeline uses q = 5)."""
+    r, W = _codes_pair(read, window, E, obstacles)
+    return int(_L().or_qgram_q(_p(r), len(r), _p(W), E, q))
+
+
+def eda(read, window, E: int, obstacles=None) -> int:
+    """SneakySnake approximation of one pair. ``window`` has len(read) + 2E bases;
+    ``obstacles`` (bool array over the window) marks bases outside the genome."""
+    r, W = _codes_pair(read, window, E, obstacles)
     return int(_L().or_eda_codes(_p(r), len(r), _p(W), E))
 
 
-def eda_batch(pairs, idx=None, threads: int = 1) -> np.ndarray:
-    """Distances for a read-versus-window pair set (``gen.EdaPairs``), optionally only for
-    the pairs ``idx``."""
+def eda_batch(pairs, idx=None, threads: int = 1, algo: int = 0) -> np.ndarray:
+    """Distances (approximation ``algo``) for a read-versus-window pair set
+    (``gen.EdaPairs``), optionally only for the pairs ``idx``."""
     if idx is None:
         n = pairs.n_pairs
         win_seq, win_off = pairs.win_seq, pairs.win_off
@@ -334,7 +358,7 @@ def eda_batch(pairs, idx=None, threads: int = 1) -> np.ndarray:
         ws = np.ascontiguousarray(win_seq[int(win_off[a]):int(win_off[b])])
         out = np.zeros(b - a, np.uint8)
         _L().or_eda_batch(_p(rs), _p(ro), _p(ws), _p(wo), _p(np.ascontiguousarray(pr[a:b])),
-                          _p(np.ascontiguousarray(E[a:b])), b - a, _p(out))
+                          _p(np.ascontiguousarray(E[a:b])), b - a, algo, _p(out))
         dist[a:b] = out
 
     shards = _shards(n, threads) if n else []

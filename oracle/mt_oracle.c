@@ -311,15 +311,127 @@ uint32_t or_eda_codes(const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E
     return cnt < E + 1 ? cnt : E + 1;
 }
 
-/* ASCII wrapper: read of n bases, window of n + 2E bases (no out-of-genome bases).
- * Returns 0xFFFFFFFF on a non-ACGT base. */
-uint32_t or_eda_ascii(const uint8_t *read, uint32_t n, const uint8_t *win, uint32_t E) {
+/* ---- the paper's other approximations on the same candidate (Table 1; the Discussion of
+ * their cost: Base Counting and q-gram compare counts in O(n), HD and SHD follow the
+ * pigeonhole principle in O(nE)). The paper gives no formulas; the readings taken:
+ *  - HD, Base Counting and q-gram compare the read r with the window's central segment
+ *    S = W[E, E + n), which starts at the location's first diagonal; a window code of 4
+ *    (outside the genome) equals no read base;
+ *  - SHD uses the 2E + 1 diagonals of SneakySnake's map.
+ * Each returns min(estimate, E + 1); a pair is accepted iff the result is <= E. */
+
+/* Hamming distance: the positions j with r[j] != S[j]. */
+uint32_t or_hd_codes(const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E) {
+    uint32_t cnt = 0;
+    for (uint32_t j = 0; j < n; j++) cnt += r[j] != W[E + j];
+    return cnt < E + 1 ? cnt : E + 1;
+}
+
+/* Base Counting: with c_r(b) and c_S(b) the number of bases b in r and in S (b = 4 only
+ * in S), one edit changes sum_b |c_r(b) - c_S(b)| by at most 2, so ceil(sum / 2) is at most
+ * the edit distance of r and S. */
+uint32_t or_bc_codes(const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E) {
+    int64_t cr[5] = {0, 0, 0, 0, 0}, cs[5] = {0, 0, 0, 0, 0};
+    for (uint32_t j = 0; j < n; j++) {
+        cr[r[j]]++;
+        cs[W[E + j]]++;
+    }
+    int64_t sum = 0;
+    for (int b = 0; b < 5; b++) sum += cr[b] > cs[b] ? cr[b] - cs[b] : cs[b] - cr[b];
+    uint64_t est = (uint64_t)(sum + 1) / 2;
+    return est < E + 1 ? (uint32_t)est : E + 1;
+}
+
+/* q-gram distance (Ukkonen's lemma): with P_r(g) and P_S(g) the occurrences of the q-long
+ * string g in r and in S, one edit changes sum_g |P_r(g) - P_S(g)| by at most 2q, so
+ * ceil(sum / 2q) is at most the edit distance of r and S. A q-gram of S holding an
+ * out-of-genome base occurs in no read and adds 1 to the sum. n < q: no q-grams, 0.
+ * q in [1, 8]; 0xFFFFFFFF otherwise or when out of memory. */
+uint32_t or_qgram_q(const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E, uint32_t q) {
+    if (q == 0 || q > 8) return 0xFFFFFFFFu;
+    if (n < q) return 0;
+    const size_t B = (size_t)1 << (2 * q);
+    int64_t *P = calloc(B, sizeof(int64_t));
+    if (!P) return 0xFFFFFFFFu;
+    int64_t sum = 0;
+    for (uint32_t j = 0; j + q <= n; j++) {
+        size_t g = 0;
+        for (uint32_t t = 0; t < q; t++) g |= (size_t)r[j + t] << (2 * t);
+        P[g]++;
+    }
+    for (uint32_t j = 0; j + q <= n; j++) {
+        size_t g = 0;
+        int outside = 0;
+        for (uint32_t t = 0; t < q; t++) {
+            uint8_t b = W[E + j + t];
+            if (b == 4) outside = 1;
+            else g |= (size_t)b << (2 * t);
+        }
+        if (outside) sum++;
+        else P[g]--;
+    }
+    for (size_t g = 0; g < B; g++) sum += P[g] < 0 ? -P[g] : P[g];
+    free(P);
+    uint64_t est = (uint64_t)(sum + 2 * q - 1) / (2 * q);
+    return est < E + 1 ? (uint32_t)est : E + 1;
+}
+
+uint32_t or_qgram_codes(const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E) {
+    return or_qgram_q(r, n, W, E, 5);
+}
+
+/* Shifted Hamming distance: for each diagonal d in [-E, E] the mismatch mask
+ * H_d(j) = [r[j] != W[E + j + d]]; a run of one or two matches with a mismatch on both
+ * sides is taken as a chance match and set to mismatches; the masks are AND-ed over the
+ * diagonals and the mismatches left are counted. 0xFFFFFFFF when out of memory. */
+uint32_t or_shd_codes(const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E) {
+    uint8_t *F = malloc(n ? n : 1), *H = malloc(n ? n : 1);
+    if (!F || !H) { free(F); free(H); return 0xFFFFFFFFu; }
+    memset(F, 1, n ? n : 1);
+    for (int64_t d = -(int64_t)E; d <= (int64_t)E; d++) {
+        for (uint32_t j = 0; j < n; j++) H[j] = r[j] != W[(int64_t)E + (int64_t)j + d];
+        uint32_t j = 0;
+        while (j < n) {
+            if (H[j]) { j++; continue; }
+            uint32_t a = j;
+            while (j < n && !H[j]) j++;            /* matches [a, j) */
+            if (a > 0 && j < n && j - a <= 2)
+                for (uint32_t t = a; t < j; t++) H[t] = 1;
+        }
+        for (uint32_t t = 0; t < n; t++) F[t] &= H[t];
+    }
+    uint32_t cnt = 0;
+    for (uint32_t t = 0; t < n; t++) cnt += F[t];
+    free(F); free(H);
+    return cnt < E + 1 ? cnt : E + 1;
+}
+
+/* Approximation `algo` of one candidate: 0 SneakySnake, 1 HD, 2 Base Counting, 3 q-gram
+ * (q = 5), 4 SHD; 0xFFFFFFFF for another algo. */
+uint32_t or_approx_codes(uint32_t algo, const uint8_t *r, uint32_t n, const uint8_t *W, uint32_t E) {
+    switch (algo) {
+        case 0: return or_eda_codes(r, n, W, E);
+        case 1: return or_hd_codes(r, n, W, E);
+        case 2: return or_bc_codes(r, n, W, E);
+        case 3: return or_qgram_codes(r, n, W, E);
+        case 4: return or_shd_codes(r, n, W, E);
+        default: return 0xFFFFFFFFu;
+    }
+}
+
+/* ASCII wrappers: read of n bases, window of n + 2E bases (no out-of-genome bases).
+ * Return 0xFFFFFFFF on a non-ACGT base. */
+uint32_t or_approx_ascii(uint32_t algo, const uint8_t *read, uint32_t n, const uint8_t *win, uint32_t E) {
     uint8_t *r = malloc(n ? n : 1), *W = malloc(n + 2 * E ? n + 2 * E : 1);
     uint32_t out = 0xFFFFFFFFu;
     if (r && W && to_codes(read, n, r) == OR_OK && to_codes(win, n + 2 * E, W) == OR_OK)
-        out = or_eda_codes(r, n, W, E);
+        out = or_approx_codes(algo, r, n, W, E);
     free(r); free(W);
     return out;
+}
+
+uint32_t or_eda_ascii(const uint8_t *read, uint32_t n, const uint8_t *win, uint32_t E) {
+    return or_approx_ascii(0, read, n, win, E);
 }
 
 /* A batch of read-versus-window pairs (the EDA stage alone): pair p compares read
@@ -327,12 +439,12 @@ uint32_t or_eda_ascii(const uint8_t *read, uint32_t n, const uint8_t *win, uint3
  * dist[p] = the approximation, or 0xFF for malformed input. */
 int or_eda_batch(const uint8_t *read_seq, const uint64_t *read_off, const uint8_t *win_seq,
                  const uint64_t *win_off, const uint32_t *pair_read, const uint16_t *E,
-                 uint64_t n_pairs, uint8_t *dist) {
+                 uint64_t n_pairs, uint32_t algo, uint8_t *dist) {
     for (uint64_t p = 0; p < n_pairs; p++) {
         uint64_t r = pair_read[p];
         uint32_t n = (uint32_t)(read_off[r + 1] - read_off[r]);
         if (win_off[p + 1] - win_off[p] != (uint64_t)n + 2u * E[p]) { dist[p] = 0xFF; continue; }
-        uint32_t d = or_eda_ascii(read_seq + read_off[r], n, win_seq + win_off[p], E[p]);
+        uint32_t d = or_approx_ascii(algo, read_seq + read_off[r], n, win_seq + win_off[p], E[p]);
         dist[p] = d == 0xFFFFFFFFu ? 0xFF : (uint8_t)d;
     }
     return OR_OK;
@@ -394,9 +506,9 @@ static uint32_t edit_threshold(uint64_t n, uint32_t e_abs, uint32_t e_permille) 
  * to. Returns OR_OK, OR_EINVAL (bad base / params) or OR_ENOMEM. */
 int or_map_reads(const or_index *ix, const uint8_t *reads, const uint64_t *roff, uint64_t n_reads,
                  uint32_t max_occ, uint32_t e_abs, uint32_t e_permille, uint32_t min_seeds,
-                 uint32_t top_n, const uint8_t *keep, int32_t *taxon, or_loc *locs, uint8_t *nloc,
-                 int32_t *multi, uint64_t *U) {
-    if (top_n < 1) return OR_EINVAL;
+                 uint32_t top_n, uint32_t algo, const uint8_t *keep, int32_t *taxon, or_loc *locs,
+                 uint8_t *nloc, int32_t *multi, uint64_t *U) {
+    if (top_n < 1 || algo > 4) return OR_EINVAL;
     const uint32_t k = ix->k;
     for (uint64_t r = 0; r < n_reads; r++) {
         uint64_t n = roff[r + 1] - roff[r];
@@ -480,7 +592,8 @@ int or_map_reads(const or_index *ix, const uint8_t *reads, const uint64_t *roff,
                 W[x] = (gp >= 0 && gp < glen) ? gc[gp] : 4;
             }
             for (uint64_t j = 0; j < n; j++) rr[j] = q->rel ? (uint8_t)(3 - c[n - 1 - j]) : c[j];
-            uint32_t dist = or_eda_codes(rr, (uint32_t)n, W, E);
+            uint32_t dist = or_approx_codes(algo, rr, (uint32_t)n, W, E);
+            if (dist == 0xFFFFFFFFu) { free(rr); free(W); free(cl); free(hits); free(c); free(code); free(pos); free(strand); return OR_ENOMEM; }
             or_loc *L = &locs[r * top_n + t];
             L->wstart = wstart;
             L->genome = (int32_t)q->g;

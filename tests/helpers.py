@@ -10,7 +10,9 @@ ABUND_TOL = 1e-6     # absolute; every other output must match bit for bit
 
 def oracle_params(prm: dict) -> dict:
     keys = ("max_occ", "e_abs", "e_permille", "min_seeds", "top_n", "cont_num", "cont_den", "abund_cutoff")
-    return oracle.params(**{k: prm[k] for k in keys if k in prm})
+    p = oracle.params(**{k: prm[k] for k in keys if k in prm})
+    p["eda_algo"] = (prm.get("eda_mode", 0) >> 4) & 15   # the library's mode: form | algorithm << 4
+    return p
 
 
 def as_np(x):
