@@ -209,6 +209,10 @@ def timed_steps(fn, steps, warmup, stream, torch):
     return e0.elapsed_time(e1) / steps, outs
 
 
+# the paper's other approximations (Table 1), measured beside SneakySnake
+EDA_OTHERS = (("hamming", 0x10), ("base_counting", 0x20), ("qgram", 0x30), ("shd", 0x40))
+
+
 def eda_stage(mt, torch, n_pairs, steps, warmup):
     c3 = gen.config(3)
     t0 = time.time()
@@ -236,12 +240,19 @@ def eda_stage(mt, torch, n_pairs, steps, warmup):
     same = bool(torch.equal(outs["batched"], outs["plain"]))
     accepted = float((outs["batched"].cpu().numpy() <= pairs.E).mean())
     window_bytes = int(pairs.win_off[-1])
+    # the other approximations on the same pairs, batched form
+    others = {}
+    for name, bits in EDA_OTHERS:
+        ms, o = timed_steps(lambda: mt.eda_batch(rw, ro, ww, wo, pr, E, mode=bits | mt.MT_EDA_BATCHED), steps,
+                            warmup, stream, torch)
+        others[name] = {"pairs_per_s": pairs.n_pairs / (ms / 1000.0), "ms": ms,
+                        "accepted_frac": float((o[-1].cpu().numpy() <= pairs.E).mean())}
     return {"workload": "batching: %d read-vs-window pairs, n~U[100,250], E in {2,4,6,10}%% of n, "
                         "geometric(6) candidates per read, %d reads" % (pairs.n_pairs, pairs.n_reads),
             "pairs_per_s_batched": res["batched"], "pairs_per_s_plain": res["plain"],
             "ms_batched": res["ms_batched"], "ms_plain": res["ms_plain"],
             "batched_over_plain": res["batched"] / res["plain"], "identical": same,
-            "accepted_frac": accepted, "window_bases": window_bytes}
+            "accepted_frac": accepted, "window_bases": window_bytes, "other_approximations": others}
 
 
 def serving_sample(mt, ix, reads, c, seconds, torch):
@@ -407,6 +418,18 @@ def run_ours(args):
     h2d = n_bases + (n_reads + 1) * 8
     d2h = n_reads * (4 + 1 + 24 * top_n) + G * 16
 
+    # whole classification with each other approximation (batched form, same inputs)
+    approx = {}
+    if rank == 0 and world == 1:
+        for name, bits in EDA_OTHERS:
+            prm = dict(params(c, mt.MT_EDA_BATCHED), eda_mode=bits | mt.MT_EDA_BATCHED)
+            fn = lambda: mt.classify(ix, d_reads, d_off, **prm)  # noqa: E731
+            ms_a, o = timed_steps(fn, max(1, args.steps // 2), 1, stream, torch)
+            sa = o[-1]["stats"]
+            approx[name] = {"reads_per_s": n_reads / (ms_a / 1000.0), "ms_per_step": ms_a, "ms_eda": sa["ms_eda"],
+                            "classified_frac": float((o[-1]["taxon"] >= 0).float().mean().item())}
+            del o
+
     # roofline of the dominant kernel (the seeding pass): algorithmic bytes per launch
     st = {k: statistics.mean(s[k] for s in stats) for k in stats[0]}
     seed_bytes = (n_bases                          # read bytes in
@@ -449,6 +472,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "clocks": clocks, "gpu_launches": int(st["n_launches"]) * args.steps,
             "index": {"build_s": index_s, **info},
+            "classified_frac": float((batched_out["taxon"] >= 0).float().mean().item()),
+            "other_approximations": approx,
             "counts_per_step": {k: st[k] for k in ("n_minimizers", "n_hits", "n_candidates", "n_accepted",
                                                    "n_multi", "n_fallback", "n_ext_occ", "n_stored")}}
 

@@ -70,12 +70,26 @@ typedef struct {
     uint32_t max_occ;      /* seeds with more occurrences are skipped  [1024] */
     uint32_t cont_num;     /* containment cutoff num/den on hits/max_hits  [1/10000] */
     uint32_t cont_den;
-    uint32_t eda_mode;     /* MT_EDA_BATCHED or MT_EDA_PLAIN (identical results) */
+    uint32_t eda_mode;     /* execution form | approximation (below)  [SneakySnake, batched] */
     double abund_cutoff;   /* relative abundances below this are dropped  [1e-4] */
 } mt_classify_params;
 
+/* Edit-distance approximation of each candidate, eda_mode = form | approximation.
+ * Execution forms (identical results):                                                    */
 #define MT_EDA_BATCHED 0u  /* persistent work-stealing kernel, autotuned group shape */
 #define MT_EDA_PLAIN 1u    /* one warp per pair, one launch per length bucket */
+/* Approximations (Table 1; the Discussion's O(n) count comparisons and O(nE) pigeonhole
+ * filters). Each result is min(estimate, E + 1); a location is accepted iff it is <= E.
+ * The paper gives no formulas for the last four; the readings implemented: HD, Base
+ * Counting and q-gram compare the read with the window's central segment [E, E + n) (the
+ * location's first diagonal), where a base outside the genome equals no read base.      */
+#define MT_EDA_SNAKE (0u << 4)          /* SneakySnake over the 2E+1 diagonals [48] */
+#define MT_EDA_HAMMING (1u << 4)        /* mismatches on the central segment [49] */
+#define MT_EDA_BASE_COUNTING (2u << 4)  /* ceil(sum over bases |count difference| / 2) [46] */
+#define MT_EDA_QGRAM (3u << 4)          /* ceil(q-gram profile distance / 2q), q = 5 [52] */
+#define MT_EDA_SHD (4u << 4)            /* shifted Hamming: the 2E+1 diagonal mismatch masks,
+                                           match runs of 1-2 between mismatches set to
+                                           mismatches, AND-ed; set flags counted [50] */
 
 /* One mapping location of a read (24 bytes). */
 typedef struct {
@@ -231,14 +245,16 @@ uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_bases, uint6
 int mt_pack_seqs(const uint8_t *seq, const uint64_t *offsets, uint64_t n_seqs, uint64_t *words,
                  void *stream);
 
-/* ---- edit-distance approximation stage alone (SneakySnake, Table 1 ref. [48]) ------------
+/* ---- edit-distance approximation stage alone (Table 1) ------------------------------------
  * Pair p compares read pair_read[p] (read_words: a packed set with base offsets read_off,
  * n_reads + 1 entries) with window p (win_words: a packed set with base offsets win_off,
  * n_pairs + 1 entries). Window length must equal the read length + 2 E[p]; E[p] <=
- * MT_MAX_E, read length <= MT_MAX_READ_LEN. dist[p] = min(obstacles, E[p] + 1).
- * All pointers are DEVICE pointers. mode: MT_EDA_BATCHED (one persistent work-stealing
- * launch, autotuned lanes per pair) or MT_EDA_PLAIN (one launch per read-length bucket,
- * a warp per pair); both give identical dist. The call returns after synchronising
+ * MT_MAX_E, read length <= MT_MAX_READ_LEN. dist[p] = the approximation of mode's
+ * MT_EDA_* bits, min(estimate, E[p] + 1) (SneakySnake: obstacles; window bases all count as
+ * genome bases here). All pointers are DEVICE pointers. mode = form | approximation, form
+ * MT_EDA_BATCHED (one persistent work-stealing launch, autotuned lanes per pair) or
+ * MT_EDA_PLAIN (one launch per read-length bucket, a warp per pair); both forms give
+ * identical dist. The call returns after synchronising
  * `stream`. Errors: MT_EINVAL (length mismatch, limits), MT_ENOMEM, MT_ECUDA. */
 int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
                  const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
@@ -255,6 +271,7 @@ int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off, uint64_t 
  *    the device current); make that first call before any stream capture;
  *  - every call uses the same array, so calls whose work overlaps on the GPU (other threads or
  *    streams) race and must be serialised by the caller;
+ *  - mode is the SneakySnake forms only (MT_EDA_BATCHED or MT_EDA_PLAIN);
  *  - the batched form uses lanes per pair already tuned in this process, else a default; it
  *    times nothing itself.
  * It calls no cudaMalloc, cudaFree or other allocating routine. Returns after synchronising

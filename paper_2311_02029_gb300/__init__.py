@@ -25,6 +25,10 @@ MT_XCHG_GENOME_HITS, MT_XCHG_UNIQUE, MT_XCHG_MULTI = 0, 1, 2
 # mt_allreduce_fn: int (*)(void *ctx, int kind, void *buf, uint64_t count)
 AllreduceFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64)
 MT_EDA_BATCHED, MT_EDA_PLAIN = 0, 1
+# approximations, OR-ed into eda_mode / mode with a form
+MT_EDA_SNAKE, MT_EDA_HAMMING, MT_EDA_BASE_COUNTING, MT_EDA_QGRAM, MT_EDA_SHD = 0x00, 0x10, 0x20, 0x30, 0x40
+EDA_ALGOS = {"sneakysnake": MT_EDA_SNAKE, "hamming": MT_EDA_HAMMING, "base_counting": MT_EDA_BASE_COUNTING,
+             "qgram": MT_EDA_QGRAM, "shd": MT_EDA_SHD}
 MAX_READ_LEN, MAX_E, MAX_TOPN = 1024, 127, 8
 
 LOC_DTYPE = np.dtype({"names": ["wstart", "genome", "seeds", "strand", "dist"],

@@ -25,6 +25,7 @@
 #include "internal.h"
 
 namespace mt {
+bool eda_mode_ok(uint32_t mode);
 int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *io,
                         const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
                         const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
@@ -1037,7 +1038,7 @@ int check_params(const mt_classify_params *p) {
     if (p->min_seeds < 1) return MT_EINVAL;
     if (p->max_occ > MT_MAX_OCC_LIMIT) return MT_EINVAL;
     if (p->cont_den == 0) return MT_EINVAL;
-    if (p->eda_mode != MT_EDA_BATCHED && p->eda_mode != MT_EDA_PLAIN) return MT_EINVAL;
+    if (!eda_mode_ok(p->eda_mode)) return MT_EINVAL;
     if (p->e_permille > 1000) return MT_EINVAL;
     if (p->e_permille == 0 && p->e_abs > MT_MAX_E) return MT_EINVAL;
     if (!(p->abund_cutoff >= 0.0)) return MT_EINVAL;

@@ -129,33 +129,58 @@ struct EdaPlan {
     uint64_t cap;                      // if set: class 0 holds at most `cap` items (tuning samples)
 };
 
-template <int G, class Src>
+// The approximation A of one staged pair by the G lanes of gmask; xb: the group's extra
+// shared words (q-gram histogram or SHD mask).
+template <int A, int G, bool EDGES>
+MT_DEV uint32_t approx(const uint64_t *rd, const uint64_t *wn, const PairInfo &pi, unsigned gmask, uint32_t gl,
+                       uint64_t *xb) {
+    if (A == ALGO_HD) return hamming_est<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl);
+    if (A == ALGO_BC) return basecount_est<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl);
+    if (A == ALGO_QGRAM) return qgram_est<EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, reinterpret_cast<int *>(xb));
+    if (A == ALGO_SHD)
+        return shd_est<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl, reinterpret_cast<unsigned long long *>(xb));
+    return sneaky_walk<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl);
+}
+
+// Shared words a group needs beyond the read and window for approximation A (the q-gram
+// histogram gets one word of slack so that it can start on a 16-byte boundary).
+__host__ __device__ __forceinline__ uint32_t eda_extra_words(int A, uint32_t maxn) {
+    return A == ALGO_QGRAM ? QGRAM_BINS / 2 + 1 : (A == ALGO_SHD ? (maxn + 31) / 32 + 1 : 0u);
+}
+
+template <int G, int A, class Src>
 MT_DEV void do_items(const Src &src, const uint32_t *perm, uint64_t b, uint64_t e, uint64_t *wbase,
-                     uint32_t rww, uint32_t www) {
+                     uint32_t rww, uint32_t www, uint32_t xw) {
     constexpr uint32_t groups = 32 / G;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gi = lane / G, gl = lane % G;
     const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (gi * G));
-    uint64_t *rd = wbase + (uint64_t)gi * (rww + www);
+    uint64_t *rd = wbase + (uint64_t)gi * (rww + www + xw);
     uint64_t *wn = rd + rww;
+    uint64_t *xb = wn + www;
+    if (A == ALGO_QGRAM) {   // the histogram starts at zero; each pair leaves it at zero
+        xb = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(xb) + 15) & ~static_cast<uintptr_t>(15));
+        for (uint32_t t = gl; t < QGRAM_BINS / 2; t += G) xb[t] = 0;
+        __syncwarp(gmask);
+    }
     for (uint64_t it = b + gi; it < e; it += groups) {
         uint64_t item = perm ? perm[it] : it;
         PairInfo pi = src.template stage<G>(item, rd, wn, gl);
         __syncwarp(gmask);
-        uint32_t d = pi.edges ? sneaky_walk<G, true>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl)
-                              : sneaky_walk<G, false>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl);
+        uint32_t d = pi.edges ? approx<A, G, true>(rd, wn, pi, gmask, gl, xb)
+                              : approx<A, G, false>(rd, wn, pi, gmask, gl, xb);
         if (gl == 0) src.finish(item, d);
         __syncwarp(gmask);
     }
 }
 
-template <class Src>
+template <class Src, int A>
 __global__ void __launch_bounds__(EDA_THREADS) k_eda_persistent(Src src, const uint32_t *perm, EdaPlan plan,
                                                                 unsigned long long *counter,
-                                                                uint32_t rww, uint32_t www) {
+                                                                uint32_t rww, uint32_t www, uint32_t xw) {
     extern __shared__ uint64_t sm[];
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    uint64_t *wbase = sm + (uint64_t)warp * plan.groups_max * (rww + www);
+    uint64_t *wbase = sm + (uint64_t)warp * plan.groups_max * (rww + www + xw);
     // chunk table: chunks of 128 items per class
     uint64_t pref[MAX_CLASSES + 1];
     pref[0] = 0;
@@ -177,28 +202,32 @@ __global__ void __launch_bounds__(EDA_THREADS) k_eda_persistent(Src src, const u
         uint64_t e = c == 0 ? end0 : plan.end[c];
         uint64_t b = plan.begin[c] + (id - pref[c]) * 128;
         uint64_t ee = b + 128 < e ? b + 128 : e;
+        if (A == ALGO_QGRAM) {   // one histogram per warp: a whole warp per pair
+            do_items<32, A>(src, perm, b, ee, wbase, rww, www, xw);
+            continue;
+        }
         switch (plan.G[c]) {
-            case 1: do_items<1>(src, perm, b, ee, wbase, rww, www); break;
-            case 2: do_items<2>(src, perm, b, ee, wbase, rww, www); break;
-            case 4: do_items<4>(src, perm, b, ee, wbase, rww, www); break;
-            case 8: do_items<8>(src, perm, b, ee, wbase, rww, www); break;
-            case 16: do_items<16>(src, perm, b, ee, wbase, rww, www); break;
-            default: do_items<32>(src, perm, b, ee, wbase, rww, www); break;
+            case 1: do_items<1, A>(src, perm, b, ee, wbase, rww, www, xw); break;
+            case 2: do_items<2, A>(src, perm, b, ee, wbase, rww, www, xw); break;
+            case 4: do_items<4, A>(src, perm, b, ee, wbase, rww, www, xw); break;
+            case 8: do_items<8, A>(src, perm, b, ee, wbase, rww, www, xw); break;
+            case 16: do_items<16, A>(src, perm, b, ee, wbase, rww, www, xw); break;
+            default: do_items<32, A>(src, perm, b, ee, wbase, rww, www, xw); break;
         }
     }
 }
 
 // plain form: one warp per item of [begin, end) (end from *dyn_end when given)
-template <class Src>
+template <class Src, int A>
 __global__ void __launch_bounds__(EDA_THREADS) k_eda_plain(Src src, const uint32_t *perm, uint64_t begin,
                                                            uint64_t end, const uint64_t *dyn_end,
-                                                           uint32_t rww, uint32_t www) {
+                                                           uint32_t rww, uint32_t www, uint32_t xw) {
     extern __shared__ uint64_t sm[];
     const uint32_t warp = threadIdx.x >> 5;
     uint64_t e = dyn_end ? *dyn_end : end;
     uint64_t it = begin + (uint64_t)blockIdx.x * (EDA_THREADS / 32) + warp;
     if (it >= e) return;
-    do_items<32>(src, perm, it, it + 1, sm + (uint64_t)warp * (rww + www), rww, www);
+    do_items<32, A>(src, perm, it, it + 1, sm + (uint64_t)warp * (rww + www + xw), rww, www, xw);
 }
 
 // ---- bucketing of EDA-only pairs -----------------------------------------------------------------
@@ -277,45 +306,55 @@ __global__ void k_bucket_scatter(const uint64_t *roff, const uint32_t *pair_read
 }
 
 // ---- launch helpers --------------------------------------------------------------------------------
-static size_t eda_smem(uint32_t groups_per_warp, uint32_t rww, uint32_t www) {
-    return (size_t)(EDA_THREADS / 32) * groups_per_warp * (rww + www) * 8;
+// Group shapes: words of one group (read, window, extra) for the largest pair of a launch.
+struct EdaShape {
+    uint32_t rww, www, xw;
+};
+
+static EdaShape eda_shape(int A, uint32_t maxn, uint32_t maxE) {
+    return EdaShape{eda_read_words(maxn), eda_win_words(maxn, maxE), eda_extra_words(A, maxn)};
 }
 
-template <class Src>
+static size_t eda_smem(uint32_t groups_per_warp, const EdaShape &w) {
+    return (size_t)(EDA_THREADS / 32) * groups_per_warp * (w.rww + w.www + w.xw) * 8;
+}
+
+template <int A, class Src>
 static int launch_persistent(const Src &src, const uint32_t *perm, const EdaPlan &plan,
-                             unsigned long long *counter, uint32_t rww, uint32_t www, cudaStream_t s) {
-    size_t smem = eda_smem(plan.groups_max, rww, www);
+                             unsigned long long *counter, const EdaShape &w, cudaStream_t s) {
+    size_t smem = eda_smem(plan.groups_max, w);
     if (smem > 200 * 1024) return MT_EINVAL;
     static std::mutex mu;
     {
         std::lock_guard<std::mutex> lk(mu);
-        MT_CK(cudaFuncSetAttribute(k_eda_persistent<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        MT_CK(cudaFuncSetAttribute(k_eda_persistent<Src, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     }
     int per_sm = 0;
-    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eda_persistent<Src>, EDA_THREADS, smem));
+    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eda_persistent<Src, A>, EDA_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
     unsigned grid = (unsigned)(sm_count() * per_sm);
     MT_CK(cudaMemsetAsync(counter, 0, 8, s));
-    k_eda_persistent<Src><<<grid, EDA_THREADS, smem, s>>>(src, perm, plan, counter, rww, www);
+    k_eda_persistent<Src, A><<<grid, EDA_THREADS, smem, s>>>(src, perm, plan, counter, w.rww, w.www, w.xw);
     MT_CK(cudaGetLastError());
     return MT_OK;
 }
 
-template <class Src>
+template <int A, class Src>
 static int launch_plain(const Src &src, const uint32_t *perm, uint64_t begin, uint64_t end,
-                        const uint64_t *dyn_end, uint32_t rww, uint32_t www, cudaStream_t s) {
+                        const uint64_t *dyn_end, const EdaShape &w, cudaStream_t s) {
     if (end <= begin) return MT_OK;
-    size_t smem = eda_smem(1, rww, www);
+    size_t smem = eda_smem(1, w);
+    if (smem > 200 * 1024) return MT_EINVAL;
     static std::mutex mu;
     {
         std::lock_guard<std::mutex> lk(mu);
-        MT_CK(cudaFuncSetAttribute(k_eda_plain<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        MT_CK(cudaFuncSetAttribute(k_eda_plain<Src, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     }
     uint64_t warps = end - begin;
     uint64_t blocks = (warps + EDA_THREADS / 32 - 1) / (EDA_THREADS / 32);
     while (blocks > 0) {   // grid.x is limited to 2^31-1 blocks
         uint64_t nb = std::min<uint64_t>(blocks, (1ull << 31) - 1);
-        k_eda_plain<Src><<<(unsigned)nb, EDA_THREADS, smem, s>>>(src, perm, begin, end, dyn_end, rww, www);
+        k_eda_plain<Src, A><<<(unsigned)nb, EDA_THREADS, smem, s>>>(src, perm, begin, end, dyn_end, w.rww, w.www, w.xw);
         MT_CK(cudaGetLastError());
         begin += nb * (EDA_THREADS / 32);
         blocks -= nb;
@@ -324,11 +363,13 @@ static int launch_plain(const Src &src, const uint32_t *perm, uint64_t begin, ui
 }
 
 // ---- autotuner ---------------------------------------------------------------------------------------
-// Lanes per pair for each edit-threshold class, picked by timing G in {1,2,4,8,16,32} on a
-// sample of the class the first time the class is seen in this process (per device).
+// Lanes per pair for each approximation and edit-threshold class, picked by timing G in
+// {1,2,4,8,16,32} on a sample of the class the first time the class is seen in this process
+// (per device). The q-gram approximation always takes a whole warp (one histogram per warp).
+static constexpr int N_ALGOS = 5;
 struct TuneCache {
     std::mutex mu;
-    int G[64][2 * MAX_CLASSES];   // per device: EDA-only classes, then classification classes
+    int G[64][N_ALGOS][2 * MAX_CLASSES];   // per device and algorithm: EDA-only classes, then classification classes
     TuneCache() { memset(G, 0, sizeof(G)); }
 };
 static TuneCache g_tune;
@@ -339,22 +380,21 @@ static uint32_t default_G(uint32_t E) {
     return G;
 }
 
-int tuned_G(int device, uint32_t cls, uint32_t *G) {
+static int tuned_G(int device, int algo, uint32_t cls, uint32_t *G) {
+    if (algo == ALGO_QGRAM) { *G = 32; return 1; }
     std::lock_guard<std::mutex> lk(g_tune.mu);
-    int d = device & 63;
-    *G = (uint32_t)g_tune.G[d][cls];
+    *G = (uint32_t)g_tune.G[device & 63][algo][cls];
     return *G != 0;
 }
 
-static void set_tuned_G(int device, uint32_t cls, uint32_t G) {
+static void set_tuned_G(int device, int algo, uint32_t cls, uint32_t G) {
     std::lock_guard<std::mutex> lk(g_tune.mu);
-    g_tune.G[device & 63][cls] = (int)G;
+    g_tune.G[device & 63][algo][cls] = (int)G;
 }
 
-template <class Src>
+template <int A, class Src>
 static int autotune_class(const Src &src, const uint32_t *perm, uint64_t b, uint64_t e, uint32_t cls,
-                          uint32_t rww, uint32_t www, unsigned long long *counter, cudaStream_t s,
-                          uint32_t *bestG) {
+                          const EdaShape &w, unsigned long long *counter, cudaStream_t s, uint32_t *bestG) {
     uint64_t cnt = e - b;
     uint64_t sample = std::min<uint64_t>(cnt, 1ull << 17);
     cudaEvent_t e0, e1;
@@ -371,9 +411,9 @@ static int autotune_class(const Src &src, const uint32_t *perm, uint64_t b, uint
             plan.G[0] = G;
             plan.begin[0] = b;
             plan.end[0] = b + sample;
-            if (eda_smem(plan.groups_max, rww, www) > 200 * 1024) continue;
+            if (eda_smem(plan.groups_max, w) > 200 * 1024) continue;
             MT_CK(cudaEventRecord(e0, s));
-            int rc = launch_persistent(src, perm, plan, counter, rww, www, s);
+            int rc = launch_persistent<A>(src, perm, plan, counter, w, s);
             if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
             MT_CK(cudaEventRecord(e1, s));
             MT_CK(cudaEventSynchronize(e1));
@@ -389,22 +429,17 @@ static int autotune_class(const Src &src, const uint32_t *perm, uint64_t b, uint
 }
 
 // ---- classification EDA (called by mt_classify) ------------------------------------------------
-int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *io,
-                        const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
-                        const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
-                        uint32_t maxn, uint32_t maxE, uint32_t mode, uint8_t *dist,
-                        unsigned long long *counter, cudaStream_t s, bool allow_tune) {
-    ClassifySrc src;
-    src.ix = ix; src.rw = rw; src.io = io; src.cl = cl; src.cand = cand;
-    src.top_n = top_n; src.e_abs = e_abs; src.e_permille = e_permille; src.dist = dist;
-    uint32_t rww = eda_read_words(maxn), www = eda_win_words(maxn, maxE);
-    if (mode == MT_EDA_PLAIN)
-        return launch_plain(src, nullptr, 0, max_items, cl_count, rww, www, s);
+template <int A>
+static int classify_eda(const ClassifySrc &src, uint64_t max_items, const uint64_t *cl_count, uint32_t maxn,
+                        uint32_t maxE, uint32_t form, unsigned long long *counter, cudaStream_t s,
+                        bool allow_tune) {
+    const EdaShape w = eda_shape(A, maxn, maxE);
+    if (form == MT_EDA_PLAIN) return launch_plain<A>(src, nullptr, 0, max_items, cl_count, w, s);
     int dev = 0;
     cudaGetDevice(&dev);
     const uint32_t slot = MAX_CLASSES + e_class(maxE);
     uint32_t G = 0;
-    if (!tuned_G(dev, slot, &G) && !allow_tune) G = default_G(maxE);
+    if (!tuned_G(dev, A, slot, &G) && !allow_tune) G = default_G(maxE);
     if (!G) {
         // time every lanes-per-pair choice on the first 2^17 candidates of this call
         cudaEvent_t e0, e1;
@@ -417,9 +452,9 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *
                 EdaPlan tp{};
                 tp.n_classes = 1; tp.G[0] = g; tp.groups_max = 32 / g;
                 tp.begin[0] = 0; tp.end[0] = max_items; tp.dyn_end = cl_count; tp.cap = 1ull << 17;
-                if (eda_smem(tp.groups_max, rww, www) > 96 * 1024) continue;
+                if (eda_smem(tp.groups_max, w) > 96 * 1024) continue;
                 MT_CK(cudaEventRecord(e0, s));
-                int rc = launch_persistent(src, nullptr, tp, counter, rww, www, s);
+                int rc = launch_persistent<A>(src, nullptr, tp, counter, w, s);
                 if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
                 MT_CK(cudaEventRecord(e1, s));
                 MT_CK(cudaEventSynchronize(e1));
@@ -430,7 +465,7 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        set_tuned_G(dev, slot, G);
+        set_tuned_G(dev, A, slot, G);
     }
     EdaPlan plan{};
     plan.n_classes = 1;
@@ -440,11 +475,93 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *
     plan.end[0] = max_items;
     plan.dyn_end = cl_count;
     // keep the shared-memory footprint bounded for long reads
-    while (eda_smem(plan.groups_max, rww, www) > 96 * 1024 && plan.G[0] < 32) {
+    while (eda_smem(plan.groups_max, w) > 96 * 1024 && plan.G[0] < 32) {
         plan.G[0] <<= 1;
         plan.groups_max = 32 / plan.G[0];
     }
-    return launch_persistent(src, nullptr, plan, counter, rww, www, s);
+    return launch_persistent<A>(src, nullptr, plan, counter, w, s);
+}
+
+int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *io,
+                        const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
+                        const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
+                        uint32_t maxn, uint32_t maxE, uint32_t mode, uint8_t *dist,
+                        unsigned long long *counter, cudaStream_t s, bool allow_tune) {
+    ClassifySrc src;
+    src.ix = ix; src.rw = rw; src.io = io; src.cl = cl; src.cand = cand;
+    src.top_n = top_n; src.e_abs = e_abs; src.e_permille = e_permille; src.dist = dist;
+    const uint32_t form = mode & 15u;
+    switch (mode >> 4) {
+        case ALGO_HD: return classify_eda<ALGO_HD>(src, max_items, cl_count, maxn, maxE, form, counter, s, allow_tune);
+        case ALGO_BC: return classify_eda<ALGO_BC>(src, max_items, cl_count, maxn, maxE, form, counter, s, allow_tune);
+        case ALGO_QGRAM:
+            return classify_eda<ALGO_QGRAM>(src, max_items, cl_count, maxn, maxE, form, counter, s, allow_tune);
+        case ALGO_SHD: return classify_eda<ALGO_SHD>(src, max_items, cl_count, maxn, maxE, form, counter, s, allow_tune);
+        default: return classify_eda<ALGO_SNAKE>(src, max_items, cl_count, maxn, maxE, form, counter, s, allow_tune);
+    }
+}
+
+// ---- the EDA-only batch, after bucketing ------------------------------------------------------
+template <int A>
+static int run_batch(const BatchSrc &src, const uint32_t *perm, const BucketStats &h,
+                     const unsigned long long *start, uint32_t form, unsigned long long *counter,
+                     bool allow_tune, cudaStream_t s) {
+    if (form == MT_EDA_PLAIN) {
+        for (int b = 1; b <= 32; b++) {
+            if (!h.bkt_count[b]) continue;
+            uint32_t maxn = (uint32_t)b * 32;
+            int rc = launch_plain<A>(src, perm, start[b], start[b + 1], nullptr, eda_shape(A, maxn, h.bkt_maxE[b]), s);
+            if (rc) return rc;
+        }
+        return MT_OK;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    EdaPlan plan{};
+    uint32_t minG = 32;
+    for (int c = 0; c < MAX_CLASSES; c++) {
+        if (!h.cls_count[c]) continue;
+        uint32_t G = 0;
+        if (!tuned_G(dev, A, c, &G)) {
+            if (allow_tune) {
+                int rc = autotune_class<A>(src, perm, start[c], start[c + 1], (uint32_t)c,
+                                           eda_shape(A, h.cls_maxn[c], h.cls_maxE[c]), counter, s, &G);
+                if (rc) return rc;
+                set_tuned_G(dev, A, c, G);
+            } else {
+                G = default_G(h.cls_maxE[c]);
+            }
+        }
+        uint32_t k = plan.n_classes++;
+        plan.G[k] = G;
+        plan.begin[k] = start[c];
+        plan.end[k] = start[c + 1];
+        minG = std::min(minG, G);
+    }
+    // one shared-memory layout serves every class: widen the smallest groups until it fits
+    const EdaShape w = eda_shape(A, h.maxn, h.maxE);
+    while (minG < 32 && eda_smem(32 / minG, w) > 200 * 1024) minG <<= 1;
+    for (uint32_t k = 0; k < plan.n_classes; k++) plan.G[k] = std::max(plan.G[k], minG);
+    plan.groups_max = 32 / minG;
+    return launch_persistent<A>(src, perm, plan, counter, w, s);
+}
+
+static int run_batch_algo(const BatchSrc &src, const uint32_t *perm, const BucketStats &h,
+                          const unsigned long long *start, uint32_t mode, unsigned long long *counter,
+                          bool allow_tune, cudaStream_t s) {
+    const uint32_t form = mode & 15u;
+    switch (mode >> 4) {
+        case ALGO_HD: return run_batch<ALGO_HD>(src, perm, h, start, form, counter, allow_tune, s);
+        case ALGO_BC: return run_batch<ALGO_BC>(src, perm, h, start, form, counter, allow_tune, s);
+        case ALGO_QGRAM: return run_batch<ALGO_QGRAM>(src, perm, h, start, form, counter, allow_tune, s);
+        case ALGO_SHD: return run_batch<ALGO_SHD>(src, perm, h, start, form, counter, allow_tune, s);
+        default: return run_batch<ALGO_SNAKE>(src, perm, h, start, form, counter, allow_tune, s);
+    }
+}
+
+// eda_mode / mode: execution form in the low 4 bits, approximation in bits 4-7.
+bool eda_mode_ok(uint32_t mode) {
+    return (mode & 15u) <= MT_EDA_PLAIN && (mode >> 4) < (uint32_t)N_ALGOS;
 }
 
 }  // namespace mt
@@ -454,7 +571,7 @@ using namespace mt;
 extern "C" int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
                             const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
                             const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist) {
-    if (mode != MT_EDA_BATCHED && mode != MT_EDA_PLAIN) return MT_EINVAL;
+    if (!eda_mode_ok(mode)) return MT_EINVAL;
     if (n_pairs == 0) return MT_OK;
     if (!read_words || !read_off || !win_words || !win_off || !pair_read || !E || !dist || n_reads == 0)
         return MT_EINVAL;
@@ -482,7 +599,7 @@ extern "C" int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off
     BatchSrc src;
     src.rw = read_words; src.roff = read_off; src.ww = win_words; src.woff = win_off;
     src.pair_read = pair_read; src.E = E; src.dist = dist;
-    const int by_class = mode == MT_EDA_BATCHED;
+    const int by_class = (mode & 15u) == MT_EDA_BATCHED;
     const int nkeys = by_class ? MAX_CLASSES : 33;
     std::vector<unsigned long long> start(nkeys + 1, 0);
     for (int i = 0; i < nkeys; i++) start[i + 1] = start[i] + (by_class ? h.cls_count[i] : h.bkt_count[i]);
@@ -493,40 +610,8 @@ extern "C" int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off
         if (!cuda_ok(cudaGetLastError(), "k_bucket_scatter")) { cleanup(); return MT_ECUDA; }
     }
     unsigned long long *counter = cursor + 48;
-    if (mode == MT_EDA_PLAIN) {
-        for (int b = 1; b <= 32; b++) {
-            if (!h.bkt_count[b]) continue;
-            uint32_t maxn = (uint32_t)b * 32;
-            rc = launch_plain(src, perm, start[b], start[b + 1], nullptr, eda_read_words(maxn),
-                              eda_win_words(maxn, h.bkt_maxE[b]), s);
-            if (rc) { cleanup(); return rc; }
-        }
-    } else {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        EdaPlan plan{};
-        uint32_t minG = 32;
-        for (int c = 0; c < MAX_CLASSES; c++) {
-            if (!h.cls_count[c]) continue;
-            uint32_t G = 0;
-            if (!tuned_G(dev, c, &G)) {
-                rc = autotune_class(src, perm, start[c], start[c + 1], (uint32_t)c,
-                                    eda_read_words(h.cls_maxn[c]), eda_win_words(h.cls_maxn[c], h.cls_maxE[c]),
-                                    counter, s, &G);
-                if (rc) { cleanup(); return rc; }
-                set_tuned_G(dev, c, G);
-            }
-            uint32_t k = plan.n_classes++;
-            plan.G[k] = G;
-            plan.begin[k] = start[c];
-            plan.end[k] = start[c + 1];
-            minG = std::min(minG, G);
-        }
-        plan.groups_max = 32 / minG;
-        rc = launch_persistent(src, perm, plan, counter, eda_read_words(h.maxn),
-                               eda_win_words(h.maxn, h.maxE), s);
-        if (rc) { cleanup(); return rc; }
-    }
+    rc = run_batch_algo(src, perm, h, start.data(), mode, counter, true, s);
+    if (rc) { cleanup(); return rc; }
     cudaError_t e = cudaStreamSynchronize(s);
     cleanup();
     if (!cuda_ok(e, "mt_eda_batch")) return MT_ECUDA;
@@ -614,35 +699,10 @@ extern "C" int mt_eda_batch_noalloc(const uint64_t *read_words, const uint64_t *
         MT_CK(cudaGetLastError());
     }
     unsigned long long *counter = cursor + 48;
-    if (mode == MT_EDA_PLAIN) {
-        for (int b = 1; b <= 32; b++) {
-            if (!h.bkt_count[b]) continue;
-            uint32_t maxn = (uint32_t)b * 32;
-            rc = launch_plain(src, perm, start[b], start[b + 1], nullptr, eda_read_words(maxn),
-                              eda_win_words(maxn, h.bkt_maxE[b]), s);
-            if (rc) return rc;
-        }
-    } else {
-        // lanes per pair: the autotuned value when this process has one, else the default
-        // (no timing runs here, so no events are created)
-        int dev = 0;
-        cudaGetDevice(&dev);
-        EdaPlan plan{};
-        uint32_t minG = 32;
-        for (int c = 0; c < MAX_CLASSES; c++) {
-            if (!h.cls_count[c]) continue;
-            uint32_t G = 0;
-            if (!tuned_G(dev, c, &G)) G = default_G(h.cls_maxE[c]);
-            uint32_t k = plan.n_classes++;
-            plan.G[k] = G;
-            plan.begin[k] = start[c];
-            plan.end[k] = start[c + 1];
-            minG = std::min(minG, G);
-        }
-        plan.groups_max = 32 / minG;
-        rc = launch_persistent(src, perm, plan, counter, eda_read_words(h.maxn), eda_win_words(h.maxn, h.maxE), s);
-        if (rc) return rc;
-    }
+    // lanes per pair: the autotuned value when this process has one, else the default (no
+    // timing runs here, so no events are created)
+    rc = run_batch_algo(src, perm, h, start, mode, counter, false, s);
+    if (rc) return rc;
     MT_CK(cudaStreamSynchronize(s));
     return MT_OK;
 }

@@ -92,3 +92,124 @@ __host__ __device__ __forceinline__ uint32_t eda_read_words(uint32_t maxn) {
 __host__ __device__ __forceinline__ uint32_t eda_win_words(uint32_t maxn, uint32_t maxE) {
     return (maxn + 2 * maxE + 31) / 32 + 3;
 }
+
+// ---- the pipeline's other approximations (Table 1: HD [49], SHD [50]; Base Counting [46]
+// and q-gram [52], the O(n) count comparisons of the Discussion) ----------------------------
+// Readings: HD, Base Counting and q-gram compare the read with the window's central segment
+// S = window[E, E + n) (the location's first diagonal); SHD uses all 2E+1 diagonals. A window
+// base outside the genome equals no read base. Each result is min(estimate, E + 1).
+enum EdaAlgo : int { ALGO_SNAKE = 0, ALGO_HD = 1, ALGO_BC = 2, ALGO_QGRAM = 3, ALGO_SHD = 4 };
+static constexpr uint32_t QGRAM_Q = 5;
+static constexpr uint32_t QGRAM_BINS = 1u << (2 * QGRAM_Q);
+
+// Mismatch flags (bit 2t) of read columns p .. p+31 against window columns p+off .. (p < n);
+// flags of columns >= n are cleared.
+template <bool EDGES>
+MT_DEV uint64_t mism32(const uint64_t *rd, const uint64_t *wn, uint32_t p, uint32_t off, uint32_t n,
+                       int32_t lo, int32_t hi) {
+    const uint64_t x = get32(rd, p) ^ get32(wn, p + off);
+    uint64_t m = (x | (x >> 1)) & EVEN_BITS;
+    if (EDGES) m |= edge_mask((int32_t)(p + off), lo, hi);
+    if (n - p < 32) m &= (1ull << (2 * (n - p))) - 1;
+    return m;
+}
+
+// Hamming distance on the central segment; each lane of the group takes 32-column blocks.
+template <int G, bool EDGES>
+MT_DEV uint32_t hamming_est(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E, int32_t lo,
+                            int32_t hi, unsigned gmask, uint32_t glane) {
+    uint32_t cnt = 0;
+    for (uint32_t p = 32 * glane; p < n; p += 32 * G) cnt += (uint32_t)__popcll(mism32<EDGES>(rd, wn, p, E, n, lo, hi));
+    if (G > 1) cnt = __reduce_add_sync(gmask, cnt);
+    return min(cnt, E + 1);
+}
+
+// Base Counting: ceil(sum over A, C, G, T and "outside" of |count in read - count in S| / 2).
+template <int G, bool EDGES>
+MT_DEV uint32_t basecount_est(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E, int32_t lo,
+                              int32_t hi, unsigned gmask, uint32_t glane) {
+    int d0 = 0, d1 = 0, d2 = 0, d3 = 0, d4 = 0;   // read minus segment, per base (4: outside)
+    for (uint32_t p = 32 * glane; p < n; p += 32 * G) {
+        const uint32_t v = min(32u, n - p);
+        const uint64_t V = v == 32 ? EVEN_BITS : (((1ull << (2 * v)) - 1) & EVEN_BITS);
+        const uint64_t O = EDGES ? (edge_mask((int32_t)(p + E), lo, hi) & V) : 0ull;
+        const uint64_t W = V & ~O;
+        const uint64_t xr = get32(rd, p), xw = get32(wn, p + E);
+        const uint64_t rl = xr & EVEN_BITS, rh = (xr >> 1) & EVEN_BITS;
+        const uint64_t wl = xw & EVEN_BITS, wh = (xw >> 1) & EVEN_BITS;
+        d0 += __popcll(~rl & ~rh & V) - __popcll(~wl & ~wh & W);
+        d1 += __popcll(rl & ~rh & V) - __popcll(wl & ~wh & W);
+        d2 += __popcll(~rl & rh & V) - __popcll(~wl & wh & W);
+        d3 += __popcll(rl & rh & V) - __popcll(wl & wh & W);
+        d4 -= __popcll(O);
+    }
+    if (G > 1) {
+        d0 = __reduce_add_sync(gmask, d0); d1 = __reduce_add_sync(gmask, d1);
+        d2 = __reduce_add_sync(gmask, d2); d3 = __reduce_add_sync(gmask, d3);
+        d4 = __reduce_add_sync(gmask, d4);
+    }
+    const uint32_t sum = (uint32_t)(abs(d0) + abs(d1) + abs(d2) + abs(d3) + abs(d4));
+    return min((sum + 1) / 2, E + 1);
+}
+
+// q-gram distance (q = 5), a whole warp per pair: the read's q-grams add 1 and the segment's
+// subtract 1 in a shared-memory histogram `hist` (QGRAM_BINS counters, 16-byte aligned, zero
+// on entry and on return); a segment q-gram holding an outside base adds 1 directly. The
+// warp then sums |counter| over all bins (16-byte loads) and clears them. ceil(sum / 2q).
+template <bool EDGES>
+MT_DEV uint32_t qgram_est(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E, int32_t lo,
+                          int32_t hi, int *hist) {
+    const uint32_t lane = lane_id();
+    uint32_t s = 0;
+    for (uint32_t j = lane; j + QGRAM_Q <= n; j += 32) {
+        atomicAdd(&hist[(uint32_t)get32(rd, j) & (QGRAM_BINS - 1)], 1);
+        const int32_t q0 = (int32_t)(E + j);
+        if (EDGES && (q0 < lo || q0 + (int32_t)QGRAM_Q > hi)) s++;
+        else atomicAdd(&hist[(uint32_t)get32(wn, E + j) & (QGRAM_BINS - 1)], -1);
+    }
+    __syncwarp();
+    int4 *h4 = reinterpret_cast<int4 *>(hist);
+#pragma unroll
+    for (uint32_t b = lane; b < QGRAM_BINS / 4; b += 32) {
+        const int4 v = h4[b];
+        s += (uint32_t)(abs(v.x) + abs(v.y) + abs(v.z) + abs(v.w));
+        h4[b] = make_int4(0, 0, 0, 0);
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    __syncwarp();
+    return min((s + 2 * QGRAM_Q - 1) / (2 * QGRAM_Q), E + 1);
+}
+
+// SHD: each lane takes a contiguous range of the 2E+1 diagonals and walks its masks block by
+// block, keeping the neighbouring blocks for two columns of context on each side (columns
+// outside [0, n) count as matches, so runs touching an end are never filled). A match at
+// column i is filled when it is a run of one (mismatch at i-1 and i+1) or one of a run of two
+// (mismatches at i-1 and i+2, or at i-2 and i+1). Each amended mask is AND-ed into F
+// (ceil(n/32) words of shared memory); the set flags left are counted.
+template <int G, bool EDGES>
+MT_DEV uint32_t shd_est(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E, int32_t lo,
+                        int32_t hi, unsigned gmask, uint32_t glane, unsigned long long *F) {
+    const uint32_t nb = (n + 31) / 32;
+    for (uint32_t b = glane; b < nb; b += G) F[b] = EVEN_BITS;
+    __syncwarp(gmask);
+    const uint32_t ndiag = 2 * E + 1, T = (ndiag + G - 1) / G;
+    const uint32_t dlo = glane * T, dhi = min(dlo + T, ndiag);
+    for (uint32_t di = dlo; di < dhi; di++) {
+        uint64_t P = 0, C = nb ? mism32<EDGES>(rd, wn, 0, di, n, lo, hi) : 0ull;
+        for (uint32_t b = 0; b < nb; b++) {
+            const uint64_t N = b + 1 < nb ? mism32<EDGES>(rd, wn, 32 * (b + 1), di, n, lo, hi) : 0ull;
+            const uint64_t L1 = ((C << 2) | (P >> 62)) & EVEN_BITS, L2 = ((C << 4) | (P >> 60)) & EVEN_BITS;
+            const uint64_t R1 = ((C >> 2) | (N << 62)) & EVEN_BITS, R2 = ((C >> 4) | (N << 60)) & EVEN_BITS;
+            const uint64_t fill = ~C & EVEN_BITS & ((L1 & R1) | (L1 & ~R1 & R2) | (L2 & ~L1 & R1));
+            atomicAnd(&F[b], (unsigned long long)(C | fill));
+            P = C;
+            C = N;
+        }
+    }
+    __syncwarp(gmask);
+    uint32_t cnt = 0;
+    for (uint32_t b = glane; b < nb; b += G) cnt += (uint32_t)__popcll(F[b]);
+    if (G > 1) cnt = __reduce_add_sync(gmask, cnt);
+    __syncwarp(gmask);
+    return min(cnt, E + 1);
+}
