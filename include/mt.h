@@ -38,6 +38,7 @@ extern "C" {
 #define MT_ECANCELED (-5)   /* a serving request was cancelled */
 #define MT_EBUSY (-6)       /* a serving request is still in flight */
 #define MT_EXCHANGE (-7)    /* the caller's allreduce of a sharded batch failed */
+#define MT_EIO (-8)         /* a file could not be read or written, or is not a saved index */
 
 /* ---- limits ---------------------------------------------------------------------------- */
 #define MT_MAX_READ_LEN 1024u   /* bases per read (the paper targets short reads) */
@@ -151,6 +152,18 @@ int mt_version(void);
 int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
                    const mt_index_params *params, void *stream, mt_index **out);
 void mt_free_index(mt_index *ix);
+
+/* ---- index persistence (Methods, "Index Construction & Querying": the index is built once
+ * and queried many times, so building stays off the query path) ---------------------------
+ * mt_save_index writes a built index to the file `path` (created or truncated; about the
+ * index's device_bytes), copying through a pinned host buffer on `stream`. mt_load_index reads
+ * such a file onto the current device into a new index (freed with mt_free_index), identical
+ * in every query to the one saved. Files are native little-endian, with a checked header and a
+ * trailer; a file of another shape, size or version is refused.
+ * Errors: MT_EINVAL (NULL arguments), MT_EIO (open, read or write failed; not a saved index),
+ * MT_ENOMEM / MT_ECUDA (device or pinned allocation, copies). On error *out is NULL. */
+int mt_save_index(const mt_index *ix, const char *path, void *stream);
+int mt_load_index(const char *path, void *stream, mt_index **out);
 int mt_index_get_info(const mt_index *ix, mt_index_info *info);
 
 /* ---- classification of one read batch (Fig. 1 stages 1-3; "The MetaTrinity Pipeline"):

@@ -21,6 +21,7 @@ _lib = None
 
 MT_OK, MT_EINVAL, MT_ENOMEM, MT_ETIMEDOUT, MT_ECUDA, MT_ECANCELED, MT_EBUSY = 0, -1, -2, -3, -4, -5, -6
 MT_EXCHANGE = -7
+MT_EIO = -8
 MT_XCHG_GENOME_HITS, MT_XCHG_UNIQUE, MT_XCHG_MULTI = 0, 1, 2
 # mt_allreduce_fn: int (*)(void *ctx, int kind, void *buf, uint64_t count)
 AllreduceFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64)
@@ -78,6 +79,7 @@ class IndexInfo(ctypes.Structure):
 
 
 EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
+           "mt_save_index", "mt_load_index",
            "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
@@ -100,6 +102,10 @@ def lib():
         L.mt_build_index.restype = i32
         L.mt_build_index.argtypes = [vp, vp, u32, ctypes.POINTER(IndexParams), vp, ctypes.POINTER(vp)]
         L.mt_free_index.argtypes = [vp]
+        L.mt_save_index.restype = i32
+        L.mt_save_index.argtypes = [vp, ctypes.c_char_p, vp]
+        L.mt_load_index.restype = i32
+        L.mt_load_index.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
         L.mt_index_get_info.restype = i32
         L.mt_index_get_info.argtypes = [vp, ctypes.POINTER(IndexInfo)]
         L.mt_classify.restype = i32
@@ -210,6 +216,20 @@ class Index:
         inf = IndexInfo()
         _check(lib().mt_index_get_info(self._h, ctypes.byref(inf)), "mt_index_get_info")
         return {n: int(getattr(inf, n)) for n, _ in inf._fields_}
+
+    def save(self, path: str, stream=None):
+        """``mt_save_index``: write this index to ``path``."""
+        _check(lib().mt_save_index(self._h, os.fsencode(path), _stream(stream)), "mt_save_index")
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Index":
+        """``mt_load_index``: an index read from a file written by ``save``."""
+        h = ctypes.c_void_p()
+        _check(lib().mt_load_index(os.fsencode(path), _stream(stream), ctypes.byref(h)), "mt_load_index")
+        ix = cls.__new__(cls)
+        ix._h = h
+        ix.n_genomes = ix.info()["n_genomes"]
+        return ix
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

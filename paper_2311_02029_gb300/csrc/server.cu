@@ -268,6 +268,7 @@ extern "C" const char *mt_strerror(int status) {
         case MT_ECANCELED: return "cancelled";
         case MT_EBUSY: return "still in flight";
         case MT_EXCHANGE: return "the allreduce of a sharded batch failed";
+        case MT_EIO: return "file I/O failed or not a saved index";
         default: return "unknown status";
     }
 }

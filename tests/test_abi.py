@@ -76,3 +76,17 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mt, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         mt.lib()
+
+
+def test_load_index_refuses_non_index_files_without_gpu(mtlib, tmp_path):
+    """The header and size checks run before any CUDA call."""
+    L = mtlib.lib()
+    out = ctypes.c_void_p()
+    assert L.mt_load_index(str(tmp_path / "missing.idx").encode(), None, ctypes.byref(out)) == mtlib.MT_EIO
+    p = tmp_path / "junk.idx"
+    p.write_bytes(b"not an index" * 20)
+    assert L.mt_load_index(str(p).encode(), None, ctypes.byref(out)) == mtlib.MT_EIO
+    p.write_bytes(b"MTIDX\0\0\1" + bytes(200))        # right magic, bad check field
+    assert L.mt_load_index(str(p).encode(), None, ctypes.byref(out)) == mtlib.MT_EIO
+    assert not out.value
+    assert L.mt_load_index(None, None, ctypes.byref(out)) == mtlib.MT_EINVAL
