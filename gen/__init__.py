@@ -16,6 +16,8 @@ from .workloads import (  # noqa: F401
     make_eda_pairs,
     make_arrivals,
     subsample_reads,
+    Taxonomy,
+    make_taxonomy,
     ascii_of,
     revcomp_ascii,
 )

@@ -460,3 +460,33 @@ def make_arrivals(c: dict, n_batches: int | None = None, seed: int | None = None
     lo, hi = math.log10(c["batch_min"]), math.log10(c["batch_max"])
     sizes = np.round(10.0 ** rng.uniform(lo, hi, n_batches)).astype(np.int64)
     return t, sizes
+
+
+# --------------------------------------------------------------------------------------
+# Taxonomy (synthetic: the NCBI taxonomy is not available)
+# --------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Taxonomy:
+    parent: np.ndarray        # int32 per node, -1 for the root
+    rank: list                # rank name per node
+    name: list                # scientific name per node
+    taxid: np.ndarray         # int64 identifier per node
+    genome_node: np.ndarray   # uint32 leaf node of each genome
+    ranks: tuple              # the ranks present, root first
+
+
+def make_taxonomy(genomes: Genomes) -> Taxonomy:
+    """A three-rank tree over the reference: one superkingdom, a genus per clade, a species per
+    genome (clade members are the species of their clade's genus). Node 0 is the root, nodes
+    1..C the clades, nodes C+1.. the genomes; taxids are 10^6 + node."""
+    n_clades = int(genomes.clade.max()) + 1 if genomes.n else 0
+    n = 1 + n_clades + genomes.n
+    parent = np.empty(n, np.int32)
+    parent[0] = -1
+    parent[1:1 + n_clades] = 0
+    parent[1 + n_clades:] = 1 + genomes.clade
+    rank = ["superkingdom"] + ["genus"] * n_clades + ["species"] * genomes.n
+    name = ["Synthetica"] + ["Clade_%d" % i for i in range(n_clades)] + ["Genome_%d" % g for g in range(genomes.n)]
+    return Taxonomy(parent=parent, rank=rank, name=name, taxid=10 ** 6 + np.arange(n, dtype=np.int64),
+                    genome_node=(1 + n_clades + np.arange(genomes.n)).astype(np.uint32),
+                    ranks=("superkingdom", "genus", "species"))

@@ -225,6 +225,14 @@ int mt_classify_sharded(const mt_index *ix, const uint8_t *reads, uint64_t n_bas
                         int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits,
                         double *abundance, mt_stats *stats);
 
+/* ---- taxonomic roll-up of a profile (Fig. 1, 3b; "Taxonomic Profile Generation") -----------
+ * A taxonomy is a forest over n_nodes taxa given by parent[] (-1 for a root); genome g sits at
+ * node genome_node[g]. node_abundance[v] = the sum of abundance[g] over the genomes whose node
+ * is v or lies below v (genomes summed in index order). All pointers are HOST pointers; the
+ * call uses no GPU. Errors: MT_EINVAL (a node index out of range, parent links with a cycle). */
+int mt_profile_rollup(const double *abundance, uint32_t n_genomes, const uint32_t *genome_node,
+                      const int32_t *parent, uint32_t n_nodes, double *node_abundance);
+
 /* ---- batched form with a captured CUDA graph ---------------------------------------------
  * A plan holds a preallocated workspace sized for batches of up to max_reads reads,
  * max_bases bases and reads of at most max_read_len bases, and the classification kernels

@@ -79,6 +79,8 @@ def _L():
             getattr(lib, fn).argtypes = [vp, u32, vp, u32]
         lib.or_qgram_q.restype = u32
         lib.or_qgram_q.argtypes = [vp, u32, vp, u32, u32]
+        lib.or_rollup.restype = ctypes.c_int
+        lib.or_rollup.argtypes = [vp, u32, vp, vp, u32, vp]
         lib.or_approx_codes.restype = u32
         lib.or_approx_codes.argtypes = [u32, vp, u32, vp, u32]
         lib.or_map_reads.restype = ctypes.c_int
@@ -369,3 +371,15 @@ def eda_batch(pairs, idx=None, threads: int = 1, algo: int = 0) -> np.ndarray:
         with ThreadPoolExecutor(len(shards)) as ex:
             list(ex.map(run, shards))
     return dist
+
+
+def rollup(abundance, genome_node, parent) -> np.ndarray:
+    """Taxon abundances: each taxon sums the genomes in its subtree."""
+    a = np.ascontiguousarray(abundance, dtype=np.float64)
+    gn = np.ascontiguousarray(genome_node, dtype=np.uint32)
+    par = np.ascontiguousarray(parent, dtype=np.int32)
+    out = np.zeros(len(par), np.float64)
+    rc = _L().or_rollup(_p(a), len(a), _p(gn), _p(par), len(par), _p(out))
+    if rc != 0:
+        raise OracleError("or_rollup failed: %d" % rc)
+    return out

@@ -823,3 +823,39 @@ or_index *or_build_index_threads(const uint8_t *seq, const uint64_t *off, uint32
     free(bstart);
     return ix;
 }
+
+/* ---- taxonomic roll-up (Fig. 1, 3b; "Taxonomic Profile Generation") --------------------
+ * The abundance of taxon v is the sum of the abundances of the genomes that lie in v's
+ * subtree: for every taxon and every genome, the genome counts when v is found on the path
+ * from the genome's node to its root. Returns OR_EINVAL for an index out of range or a path
+ * longer than the number of nodes (a cycle). */
+int or_rollup(const double *a, uint32_t G, const uint32_t *genome_node, const int32_t *parent,
+              uint32_t T, double *out) {
+    for (uint32_t g = 0; g < G; g++)
+        if (genome_node[g] >= T) return OR_EINVAL;
+    for (uint32_t v = 0; v < T; v++)
+        if (parent[v] < -1 || parent[v] >= (int64_t)T) return OR_EINVAL;
+    for (uint32_t g = 0; g < G; g++) {          /* every genome's path reaches a root */
+        int64_t u = genome_node[g];
+        for (uint32_t steps = 0; u != -1; steps++) {
+            if (steps >= T) return OR_EINVAL;
+            u = parent[u];
+        }
+    }
+    for (uint32_t v = 0; v < T; v++) {
+        double s = 0.0;
+        for (uint32_t g = 0; g < G; g++) {
+            int64_t u = genome_node[g];
+            uint32_t steps = 0;
+            int below = 0;
+            while (u != -1) {
+                if (u == (int64_t)v) { below = 1; break; }
+                u = parent[u];
+                if (++steps > T) return OR_EINVAL;
+            }
+            if (below) s += a[g];
+        }
+        out[v] = s;
+    }
+    return OR_OK;
+}

@@ -79,7 +79,7 @@ class IndexInfo(ctypes.Structure):
 
 
 EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
-           "mt_save_index", "mt_load_index",
+           "mt_save_index", "mt_load_index", "mt_profile_rollup",
            "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
@@ -102,6 +102,8 @@ def lib():
         L.mt_build_index.restype = i32
         L.mt_build_index.argtypes = [vp, vp, u32, ctypes.POINTER(IndexParams), vp, ctypes.POINTER(vp)]
         L.mt_free_index.argtypes = [vp]
+        L.mt_profile_rollup.restype = i32
+        L.mt_profile_rollup.argtypes = [vp, u32, vp, vp, u32, vp]
         L.mt_save_index.restype = i32
         L.mt_save_index.argtypes = [vp, ctypes.c_char_p, vp]
         L.mt_load_index.restype = i32
@@ -502,3 +504,40 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---- taxonomic profile (Fig. 1, 3b) ------------------------------------------------------------
+def _as_host(x):
+    return x.cpu().numpy() if _is_torch(x) else np.asarray(x)
+
+
+def profile_rollup(abundance, genome_node, parent) -> np.ndarray:
+    """``mt_profile_rollup``: per-taxon abundance (host arrays; ``abundance`` may be a tensor)."""
+    a = np.ascontiguousarray(_as_host(abundance), dtype=np.float64)
+    gn = np.ascontiguousarray(genome_node, dtype=np.uint32)
+    par = np.ascontiguousarray(parent, dtype=np.int32)
+    out = np.zeros(len(par), np.float64)
+    _check(lib().mt_profile_rollup(_ptr(a), len(a), _ptr(gn), _ptr(par), len(par), _ptr(out)), "mt_profile_rollup")
+    return out
+
+
+def write_cami_profile(f, sample_id: str, taxonomy, node_abundance, version: str = "0.9.1"):
+    """Writes a profile in the CAMI / OPAL profiling format: a header (@SampleID, @Version,
+    @Ranks) and one row per taxon with non-zero abundance: TAXID, RANK, TAXPATH (taxids from
+    the root), TAXPATHSN (names from the root) and PERCENTAGE. ``taxonomy`` has parent, rank,
+    name, taxid and ranks (e.g. ``gen.Taxonomy``); ``f`` is a text file object."""
+    par = np.asarray(taxonomy.parent)
+    f.write("@SampleID:%s\n@Version:%s\n@Ranks:%s\n\n" % (sample_id, version, "|".join(taxonomy.ranks)))
+    f.write("@@TAXID\tRANK\tTAXPATH\tTAXPATHSN\tPERCENTAGE\n")
+    order = sorted(range(len(par)), key=lambda v: (list(taxonomy.ranks).index(taxonomy.rank[v]), v))
+    for v in order:
+        if node_abundance[v] <= 0.0:
+            continue
+        path, u = [], v
+        while u != -1:
+            path.append(int(u))
+            u = int(par[u])
+        path.reverse()
+        f.write("%d\t%s\t%s\t%s\t%.6f\n" % (int(taxonomy.taxid[v]), taxonomy.rank[v],
+                                                "|".join(str(int(taxonomy.taxid[u])) for u in path),
+                                                "|".join(taxonomy.name[u] for u in path), 100.0 * node_abundance[v]))
