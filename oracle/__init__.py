@@ -79,6 +79,7 @@ def _L():
             getattr(lib, fn).argtypes = [vp, u32, vp, u32]
         lib.or_qgram_q.restype = u32
         lib.or_qgram_q.argtypes = [vp, u32, vp, u32, u32]
+        lib.or_hpc.argtypes = [vp, vp, u64, vp, vp]
         lib.or_rollup.restype = ctypes.c_int
         lib.or_rollup.argtypes = [vp, u32, vp, vp, u32, vp]
         lib.or_approx_codes.restype = u32
@@ -130,8 +131,13 @@ def minimizers(seq, k: int, w: int, canonical: int):
 class Index:
     """The oracle's reference index: all genome minimizers sorted by k-mer code."""
 
-    def __init__(self, seq, offsets, k: int, w: int, canonical: int, threads: int = 1):
-        """``threads > 1`` builds the same index with the work split over host threads."""
+    def __init__(self, seq, offsets, k: int, w: int, canonical: int, threads: int = 1, compressed: bool = False):
+        """``threads > 1`` builds the same index with the work split over host threads.
+        ``compressed``: minimizers of the homopolymer-compressed genomes (a containment
+        index; its positions are in compressed coordinates)."""
+        self.hpc = bool(compressed)
+        if self.hpc:
+            seq, offsets = hpc(seq, offsets)
         self.seq = _u8(seq)
         self.offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
         self.G = len(self.offsets) - 1
@@ -177,9 +183,23 @@ def params(**kw) -> dict:
     return p
 
 
+def hpc(seq, offsets):
+    """Homopolymer compression of a sequence set: each run of one base becomes one base."""
+    s = _u8(seq)
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    n = len(off) - 1
+    out = np.zeros(max(1, int(off[-1] - off[0])), np.uint8)
+    out_off = np.zeros(n + 1, np.uint64)
+    _L().or_hpc(_p(s), _p(off), n, _p(out), _p(out_off))
+    return out[:int(out_off[-1])].copy(), out_off
+
+
 def count_hits(ix: Index, reads_seq, reads_off, max_occ: int, hits: np.ndarray | None = None):
+    """Seed hits per genome (containment); over compressed reads for a compressed index."""
     s = _u8(reads_seq)
     off = np.ascontiguousarray(reads_off, dtype=np.uint64)
+    if getattr(ix, "hpc", False):
+        s, off = hpc(s, off)
     if hits is None:
         hits = np.zeros(ix.G, np.uint64)
     rc = _L().or_count_hits(ix._h, _p(s), _p(off), len(off) - 1, max_occ, _p(hits))
@@ -234,25 +254,27 @@ def _slice_reads(reads_seq, reads_off, a: int, b: int):
     return reads_seq[base:int(off[-1])], off - np.uint64(base)
 
 
-def classify(ix: Index, reads_seq, reads_off, p: dict, threads: int = 1):
+def classify(ix: Index, reads_seq, reads_off, p: dict, threads: int = 1, keep=None):
     """The whole batch: containment over all reads, the kept-genome mask, mapping and the
     per-read decision, then abundances. ``threads > 1`` shards the reads over host threads
     (the per-read results do not depend on the sharding; genome hits and unique counts are
-    sums; the abundance step runs once over all reads)."""
+    sums; the abundance step runs once over all reads). A given ``keep`` mask (e.g. from a
+    separate containment index) replaces the batch's own containment mask."""
     s = _u8(reads_seq)
     off = np.ascontiguousarray(reads_off, dtype=np.uint64)
     n = len(off) - 1
     shards = _shards(n, threads) if n else []
+    given = keep
     if threads <= 1 or len(shards) <= 1:
         hits = count_hits(ix, s, off, p["max_occ"])
-        keep = keep_mask(hits, p["cont_num"], p["cont_den"])
+        keep = keep_mask(hits, p["cont_num"], p["cont_den"]) if given is None else np.asarray(given, np.uint8)
         m = map_reads(ix, s, off, p, keep)
     else:
         with ThreadPoolExecutor(len(shards)) as ex:
             parts = list(ex.map(lambda ab: count_hits(ix, *_slice_reads(s, off, *ab), p["max_occ"]),
                                 shards))
             hits = np.sum(parts, axis=0, dtype=np.uint64)
-            keep = keep_mask(hits, p["cont_num"], p["cont_den"])
+            keep = keep_mask(hits, p["cont_num"], p["cont_den"]) if given is None else np.asarray(given, np.uint8)
             ms = list(ex.map(lambda ab: map_reads(ix, *_slice_reads(s, off, *ab), p, keep), shards))
         m = dict(taxon=np.concatenate([x["taxon"] for x in ms]),
                  locs=np.concatenate([x["locs"] for x in ms]),

@@ -859,3 +859,17 @@ int or_rollup(const double *a, uint32_t G, const uint32_t *genome_node, const in
     }
     return OR_OK;
 }
+
+/* ---- homopolymer compression (the containment index's seeds: minimap2's -H, Results
+ * "Evaluation Methodology", k = 28, w = 18) ------------------------------------------------
+ * Every run of one repeated byte in a sequence becomes a single byte; runs never join across
+ * sequences. out needs off[n] - off[0] bytes; out_off gets n + 1 offsets from 0. */
+void or_hpc(const uint8_t *seq, const uint64_t *off, uint64_t n, uint8_t *out, uint64_t *out_off) {
+    uint64_t o = 0;
+    out_off[0] = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        for (uint64_t j = off[i]; j < off[i + 1]; j++)
+            if (j == off[i] || seq[j] != seq[j - 1]) out[o++] = seq[j];
+        out_off[i + 1] = o;
+    }
+}
