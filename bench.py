@@ -430,6 +430,18 @@ def run_ours(args):
                             "classified_frac": float((o[-1]["taxon"] >= 0).float().mean().item())}
             del o
 
+    # containment alone (stage 1), with this index and with the paper's containment seeds
+    # (homopolymer-compressed genomes, k = 28, w = 18)
+    contain = {}
+    if rank == 0 and world == 1:
+        hix = mt.Index(g.seq, g.offsets, 28, 18, 1, hpc=True)
+        for name, cix in (("mapping_index_k21_w11", ix), ("hpc_index_k28_w18", hix)):
+            fn = lambda: mt.containment(cix, d_reads, d_off, cont_den=10000)  # noqa: E731
+            ms_c, _ = timed_steps(fn, max(1, args.steps // 2), 1, stream, torch)
+            contain[name] = {"reads_per_s": n_reads / (ms_c / 1000.0), "ms_per_step": ms_c,
+                             "index_bytes": cix.info()["device_bytes"]}
+        hix.close()
+
     # roofline of the dominant kernel (the seeding pass): algorithmic bytes per launch
     st = {k: statistics.mean(s[k] for s in stats) for k in stats[0]}
     seed_bytes = (n_bases                          # read bytes in
@@ -474,6 +486,7 @@ def run_ours(args):
             "index": {"build_s": index_s, **info},
             "classified_frac": float((batched_out["taxon"] >= 0).float().mean().item()),
             "other_approximations": approx,
+            "containment_only": contain,
             "counts_per_step": {k: st[k] for k in ("n_minimizers", "n_hits", "n_candidates", "n_accepted",
                                                    "n_multi", "n_fallback", "n_ext_occ", "n_stored")}}
 

@@ -59,8 +59,14 @@ typedef struct {
     uint32_t k;          /* k-mer length, 1..MT_MAX_K */
     uint32_t w;          /* consecutive k-mers per window, 1..MT_MAX_W */
     uint32_t canonical;  /* 1: a k-mer and its reverse complement share one code */
-    uint32_t reserved;   /* must be 0 */
+    uint32_t flags;      /* 0, or MT_INDEX_HPC */
 } mt_index_params;
+
+/* The index holds the minimizers of the homopolymer-compressed genomes (every run of one base
+ * taken as a single base; minimap2's -H, which the paper's containment index uses with k = 28,
+ * w = 18). Such an index counts seed hits for containment (mt_containment) only; its
+ * positions are in compressed coordinates, so mt_classify refuses it. */
+#define MT_INDEX_HPC 1u
 
 /* Per-call classification parameters. Paper defaults in brackets. */
 typedef struct {
@@ -131,6 +137,8 @@ typedef struct {
     uint64_t n_keys;         /* distinct minimizer codes */
     uint64_t table_slots;    /* open-addressing slots (power of two) */
     uint64_t device_bytes;   /* HBM held by the index */
+    uint32_t flags;          /* the build's flags (MT_INDEX_HPC) */
+    uint32_t pad;
 } mt_index_info;
 
 /* ---- general ---------------------------------------------------------------------------- */
@@ -188,11 +196,36 @@ int mt_index_get_info(const mt_index *ix, mt_index_info *info);
  *   nloc[n_reads]; locs[n_reads * top_n] (unused slots have genome -1);
  *   genome_hits[n_genomes] (stage-1 counts); abundance[n_genomes]; stats.
  * Errors: MT_EINVAL (bad base, read longer than MT_MAX_READ_LEN, bad offsets, parameter
- *   out of range), MT_ENOMEM, MT_ECUDA. */
+ *   out of range, an index built with MT_INDEX_HPC), MT_ENOMEM, MT_ECUDA. */
 int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
                 const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
                 int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
                 uint64_t *genome_hits, double *abundance, mt_stats *stats);
+
+/* ---- containment alone (Fig. 1 stage 1; "The MetaTrinity Pipeline") ------------------------
+ * Seed hits per genome over the batch, counted with multiplicity for every minimizer of every
+ * read that has at most max_occ occurrences, and the kept-genome mask
+ * keep[g] = (hits[g] * cont_den > max_h hits[h] * cont_num). With an index built with
+ * MT_INDEX_HPC the reads' minimizers are taken after homopolymer compression (the paper's
+ * containment index: minimap2's -H, k = 28, w = 18). reads / offsets / device_ptrs as in
+ * mt_classify; genome_hits[n_genomes] and keep[n_genomes] (keep may be NULL) are host or device
+ * pointers like the inputs. Returns after synchronising `stream`.
+ * Errors: MT_EINVAL (bad base, bad offsets, read longer than MT_MAX_READ_LEN, max_occ above
+ * MT_MAX_OCC_LIMIT, cont_den 0), MT_ENOMEM, MT_ECUDA. */
+int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                   uint64_t n_reads, uint32_t max_occ, uint32_t cont_num, uint32_t cont_den,
+                   int device_ptrs, void *stream, uint64_t *genome_hits, uint8_t *keep);
+
+/* mt_classify with a given kept-genome mask: read mapping and profiling (stages 2 and 3) over
+ * the genomes g with keep[g] != 0 -- e.g. the mask mt_containment computes with a separate
+ * containment index, the paper's subset database -- instead of the batch's own containment
+ * cutoff (params->cont_num / cont_den are not used). genome_hits still reports this index's seed
+ * hits. keep: n_genomes bytes, a host or device pointer like the inputs. Errors: those of
+ * mt_classify; MT_EINVAL for a NULL keep. */
+int mt_classify_masked(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
+                       const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
+                       int device_ptrs, void *stream, const uint8_t *keep, int32_t *taxon, uint8_t *nloc,
+                       mt_loc *locs, uint64_t *genome_hits, double *abundance, mt_stats *stats);
 
 /* ---- one batch sharded over several processes (ranks) -------------------------------------
  * Stages 1 and 3 are defined over the whole batch: the containment cutoff compares a genome's

@@ -22,6 +22,7 @@ _lib = None
 MT_OK, MT_EINVAL, MT_ENOMEM, MT_ETIMEDOUT, MT_ECUDA, MT_ECANCELED, MT_EBUSY = 0, -1, -2, -3, -4, -5, -6
 MT_EXCHANGE = -7
 MT_EIO = -8
+MT_INDEX_HPC = 1
 MT_XCHG_GENOME_HITS, MT_XCHG_UNIQUE, MT_XCHG_MULTI = 0, 1, 2
 # mt_allreduce_fn: int (*)(void *ctx, int kind, void *buf, uint64_t count)
 AllreduceFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64)
@@ -48,7 +49,7 @@ class MtError(RuntimeError):
 
 class IndexParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_uint32), ("w", ctypes.c_uint32), ("canonical", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32)]
 
 
 class ClassifyParams(ctypes.Structure):
@@ -75,12 +76,13 @@ class IndexInfo(ctypes.Structure):
     _fields_ = [("n_genomes", ctypes.c_uint32), ("k", ctypes.c_uint32), ("w", ctypes.c_uint32),
                 ("canonical", ctypes.c_uint32), ("total_bases", ctypes.c_uint64),
                 ("n_occ", ctypes.c_uint64), ("n_keys", ctypes.c_uint64),
-                ("table_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+                ("table_slots", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
            "mt_save_index", "mt_load_index", "mt_profile_rollup",
-           "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_classify_workspace_bytes", "mt_pack_seqs",
+           "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_containment", "mt_classify_masked", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
            "mt_server_cancel", "mt_server_destroy"]
@@ -113,6 +115,11 @@ def lib():
         L.mt_classify.restype = i32
         L.mt_classify.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
                                   vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
+        L.mt_containment.restype = i32
+        L.mt_containment.argtypes = [vp, vp, u64, vp, u64, u32, u32, u32, i32, vp, vp, vp]
+        L.mt_classify_masked.restype = i32
+        L.mt_classify_masked.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
+                                         vp, vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.mt_classify_sharded.restype = i32
         L.mt_classify_sharded.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
                                           AllreduceFn, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
@@ -200,11 +207,12 @@ def _host_u64(a) -> np.ndarray:
 class Index:
     """Device-resident reference index (``mt_build_index``). Genomes are host bytes."""
 
-    def __init__(self, genomes, offsets, k: int, w: int, canonical: int = 1, stream=None):
+    def __init__(self, genomes, offsets, k: int, w: int, canonical: int = 1, stream=None, hpc: bool = False):
+        """``hpc``: index the homopolymer-compressed genomes (a containment index)."""
         g = _host_u8(genomes)
         off = _host_u64(offsets)
         self.n_genomes = len(off) - 1
-        p = IndexParams(k, w, canonical, 0)
+        p = IndexParams(k, w, canonical, MT_INDEX_HPC if hpc else 0)
         h = ctypes.c_void_p()
         _check(lib().mt_build_index(_ptr(g), _ptr(off), self.n_genomes, ctypes.byref(p),
                                     _stream(stream), ctypes.byref(h)), "mt_build_index")
@@ -251,14 +259,20 @@ def classify_params(e_abs=0, e_permille=100, min_seeds=3, top_n=3, max_occ=1024,
                           abund_cutoff)
 
 
-def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params) -> dict:
-    """Marshalling shared by ``classify`` and ``classify_sharded`` (cb: an AllreduceFn or None)."""
+def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params, keep=None) -> dict:
+    """Marshalling shared by ``classify``, ``classify_sharded`` (cb: an AllreduceFn) and
+    ``classify_masked`` (keep: the genome mask)."""
     p = classify_params(**params)
     st = Stats()
     G = ix.n_genomes
 
     def call(rptr, nb, optr, n_reads, dev):
         L = lib()
+        if keep is not None:
+            k = keep if dev else np.ascontiguousarray(_as_host(keep), dtype=np.uint8)
+            return L.mt_classify_masked(ix.handle, rptr, nb, optr, n_reads, ctypes.byref(p), dev, _stream(stream),
+                                        _ptr(k), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                        _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st))
         if cb is None:
             return L.mt_classify(ix.handle, rptr, nb, optr, n_reads, ctypes.byref(p), dev, _stream(stream),
                                  _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
@@ -288,7 +302,7 @@ def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params) -> 
         else:
             out = dict(out)
         rc = call(_ptr(r), len(r), _ptr(off), n_reads, 0)
-    _check(rc, "mt_classify" if cb is None else "mt_classify_sharded")
+    _check(rc, "mt_classify_masked" if keep is not None else ("mt_classify" if cb is None else "mt_classify_sharded"))
     out["stats"] = st.as_dict()
     return out
 
@@ -298,6 +312,33 @@ def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None
     (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors).
     ``out`` may hold preallocated host output arrays (e.g. in pinned memory)."""
     return _classify(ix, reads, offsets, None, stream, want_locs, out, params)
+
+
+def classify_masked(ix: Index, reads, offsets, keep, *, stream=None, want_locs=True, out=None, **params) -> dict:
+    """``mt_classify_masked``: mapping and profiling over the genomes with ``keep`` != 0 (a
+    uint8 array of n_genomes; a CUDA tensor when the reads are)."""
+    return _classify(ix, reads, offsets, None, stream, want_locs, out, params, keep=keep)
+
+
+def containment(ix: Index, reads, offsets, *, max_occ=1024, cont_num=1, cont_den=10000, stream=None) -> dict:
+    """``mt_containment``: seed hits per genome and the kept-genome mask of a batch (host
+    arrays, or CUDA tensors in and out)."""
+    G = ix.n_genomes
+    if _is_torch(reads) and reads.is_cuda:
+        import torch
+        hits = torch.empty(G, dtype=torch.int64, device=reads.device)
+        keep = torch.empty(G, dtype=torch.uint8, device=reads.device)
+        rc = lib().mt_containment(ix.handle, _ptr(reads), reads.numel(), _ptr(offsets), offsets.numel() - 1, max_occ,
+                                  cont_num, cont_den, 1, _stream(stream), _ptr(hits), _ptr(keep))
+    else:
+        r = _host_u8(reads)
+        off = _host_u64(offsets)
+        hits = np.empty(G, np.uint64)
+        keep = np.empty(G, np.uint8)
+        rc = lib().mt_containment(ix.handle, _ptr(r), len(r), _ptr(off), len(off) - 1, max_occ, cont_num, cont_den,
+                                  0, _stream(stream), _ptr(hits), _ptr(keep))
+    _check(rc, "mt_containment")
+    return dict(genome_hits=hits, keep=keep)
 
 
 def allreduce_callback(fn) -> AllreduceFn:

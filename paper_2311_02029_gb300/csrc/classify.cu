@@ -163,12 +163,56 @@ MT_DEV bool warp_pack(const uint8_t *reads, uint64_t n_bases, int vec_ok, uint64
         if ((lane & 3u) == 0 && t < nw) {
             const uint64_t word = (uint64_t)v | ((uint64_t)hi << 32);
             rd[t] = word;
-            dst[t] = word;
+            if (dst) dst[t] = word;
         }
     }
     if (lane < 2) rd[nw + lane] = 0;
     __syncwarp();
     return __any_sync(FULL, bad);
+}
+
+// Homopolymer compression of a packed read in place (the containment seeds of an index built
+// with MT_INDEX_HPC): each run of one base becomes a single base. Pass t reads word t: a lane
+// keeps base 32t+lane when it differs from the base before it, a ballot gives the kept
+// bases' output positions, and each output word is assembled with redux OR; an output word is
+// stored once complete, at an index <= t, so no word is written before it has been read.
+// Zeroes the words after the result (up to the old end + 2). Returns the new length.
+MT_DEV uint32_t warp_hpc(uint64_t *rd, uint32_t n) {
+    const uint32_t lane = lane_id();
+    const uint32_t nw = (n + 31) / 32;
+    uint32_t out = 0, prev = 4;   // bases kept so far; last base of the previous word (4: none)
+    uint64_t acc = 0;              // the output word being filled
+    for (uint32_t t = 0; t < nw; t++) {
+        const uint64_t word = rd[t];
+        __syncwarp();
+        const uint32_t b = (uint32_t)(word >> (2 * lane)) & 3u;
+        uint32_t pb = __shfl_up_sync(FULL, b, 1);
+        if (lane == 0) pb = prev;
+        const bool keep = 32 * t + lane < n && b != pb;
+        const unsigned bal = __ballot_sync(FULL, keep);
+        const uint32_t o = out + __popc(bal & ((1u << lane) - 1u));
+        const uint32_t cur = out >> 5;
+        uint64_t lo = 0, hi = 0;
+        if (keep) {
+            if ((o >> 5) == cur) lo = (uint64_t)b << (2 * (o & 31));
+            else hi = (uint64_t)b << (2 * (o & 31));
+        }
+        acc |= ((uint64_t)__reduce_or_sync(FULL, (uint32_t)(lo >> 32)) << 32) | __reduce_or_sync(FULL, (uint32_t)lo);
+        const uint64_t nxt = ((uint64_t)__reduce_or_sync(FULL, (uint32_t)(hi >> 32)) << 32) |
+                             __reduce_or_sync(FULL, (uint32_t)hi);
+        const uint32_t cnt = __popc(bal);
+        if (((out + cnt) >> 5) != cur) {   // word cur is complete
+            if (lane == 0) rd[cur] = acc;
+            acc = nxt;
+        }
+        out += cnt;
+        prev = __shfl_sync(FULL, b, 31);
+    }
+    if (lane == 0) rd[out >> 5] = acc;
+    __syncwarp();
+    for (uint32_t t = (out >> 5) + 1 + lane; t < nw + 2; t += 32) rd[t] = 0;
+    __syncwarp();
+    return out;
 }
 
 template <typename T>
@@ -300,7 +344,10 @@ MT_DEV void sort_hits(T *h, uint32_t H) {
     }
 }
 
-template <bool SMEM_HIST, bool HK32>
+// COUNT: containment only (every occurrence of every minimizer counted per genome, no
+// locations, no outputs per read); HPC: the reads' seeds are taken after homopolymer
+// compression (an index built with MT_INDEX_HPC).
+template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false>
 __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
     using HitT = typename HitKey<HK32>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -324,28 +371,30 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
     for (uint64_t r = (uint64_t)blockIdx.x * SEED_WARPS + warp; r < io.n_reads; r += total_warps) {
         const uint64_t start = io.roff[r], end = io.roff[r + 1];
         if (end < start || end > io.n_bases) {
-            if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_OFFSETS); A.qcnt[r] = 0; }
+            if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_OFFSETS); if (!COUNT) A.qcnt[r] = 0; }
             continue;
         }
         const uint64_t n64 = end - start;
         if (n64 > io.max_len) {
-            if (lane == 0) { atomicOr(&A.ctr->err, ERR_READ_TOO_LONG); A.qcnt[r] = 0; }
+            if (lane == 0) { atomicOr(&A.ctr->err, ERR_READ_TOO_LONG); if (!COUNT) A.qcnt[r] = 0; }
             continue;
         }
-        const uint32_t n = (uint32_t)n64;
+        uint32_t n = (uint32_t)n64;
         // packed read, also kept in rw for the approximation stage
-        if (warp_pack(io.reads, io.n_bases, io.vec_ok, start, n, ws.rd, A.rw + seq_word(start, io.off0, r))) {
-            if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_BASE); A.qcnt[r] = 0; }
+        if (warp_pack(io.reads, io.n_bases, io.vec_ok, start, n, ws.rd,
+                      COUNT ? nullptr : A.rw + seq_word(start, io.off0, r))) {
+            if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_BASE); if (!COUNT) A.qcnt[r] = 0; }
             continue;
         }
+        if (HPC) n = warp_hpc(ws.rd, n);
         const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
         if (n < k || n - k + 1 < w) {
-            if (lane == 0) A.qcnt[r] = 0;
+            if (lane == 0 && !COUNT) A.qcnt[r] = 0;
             continue;
         }
         const uint32_t nwin = n - k - w + 2, nk = n - k;
         uint32_t H = 0;
-        bool ovf = false;
+        bool ovf = COUNT;   // counting only from the start
         int32_t carry = -1;
         for (uint32_t t0 = 0; t0 < nwin; t0 += TILE) {
             const uint32_t tw = min(TILE, nwin - t0);
@@ -521,6 +570,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             __syncwarp();
         }
         n_hits += H;
+        if (COUNT) continue;
         if (ovf) {
             if (lane == 0) {
                 A.qcnt[r] = QOVF;
@@ -1065,6 +1115,8 @@ struct EnqueueCtx {
     uint64_t launches;
     mt_allreduce_fn xfn;   // sum over the ranks of a sharded batch, or null
     void *xctx;
+    const uint8_t *keep_in;   // a caller's genome mask replacing the containment mask, or null
+    bool keep_dev;            // keep_in is a device pointer
 };
 
 // Replaces the G-vector at `dev` with its sum over the ranks of a sharded batch (a no-op for an
@@ -1080,14 +1132,14 @@ static int exchange(const EnqueueCtx &c, cudaStream_t s, void *dev, uint32_t G, 
     return MT_OK;
 }
 
-template <bool SH, bool HK32>
+template <bool SH, bool HK32, bool COUNT = false, bool HPC = false>
 static int launch_seed(const SeedArgs &A, size_t smem, uint64_t need, cudaStream_t s) {
-    MT_CK(cudaFuncSetAttribute(k_seed<SH, HK32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MT_CK(cudaFuncSetAttribute(k_seed<SH, HK32, COUNT, HPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<SH, HK32>, SEED_THREADS, smem));
+    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<SH, HK32, COUNT, HPC>, SEED_THREADS, smem));
     per_sm = std::max(per_sm, 1);
     const unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
-    k_seed<SH, HK32><<<grid, SEED_THREADS, smem, s>>>(A);
+    k_seed<SH, HK32, COUNT, HPC><<<grid, SEED_THREADS, smem, s>>>(A);
     MT_CK(cudaGetLastError());
     return MT_OK;
 }
@@ -1131,8 +1183,12 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         mark(1);
         if ((rc = exchange(c, s, ghits, G, MT_XCHG_GENOME_HITS))) return rc;
 
-        k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
-        MT_CK(cudaGetLastError());
+        if (c.keep_in) {
+            MT_CK(cudaMemcpyAsync(P(L.keep), c.keep_in, G, c.keep_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+        } else {
+            k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
+            MT_CK(cudaGetLastError());
+        }
         const unsigned rblocks = (unsigned)std::min<uint64_t>((c.cap_reads + 255) / 256, (uint64_t)sm_count() * 8);
         k_select<<<rblocks, 256, 0, s>>>(io, A.qcnt, A.clus, (const uint8_t *)P(L.keep), top_n, (Cluster *)P(L.cand),
                                          (uint8_t *)P(L.nloc_ws), (uint32_t *)P(L.cl), A.fb_list, ctr);
@@ -1242,9 +1298,11 @@ extern "C" uint64_t mt_classify_workspace_bytes(const mt_index *ix, uint64_t n_b
 
 static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
                          uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
-                         mt_allreduce_fn xfn, void *xctx, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
-                         uint64_t *genome_hits, double *abundance, mt_stats *stats) {
+                         mt_allreduce_fn xfn, void *xctx, const uint8_t *keep_in, int32_t *taxon,
+                         uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
+                         mt_stats *stats) {
     if (!ix || !offsets || (!taxon && n_reads) || (!reads && n_bases)) return MT_EINVAL;
+    if (ix->hpc) return MT_EINVAL;   // a containment index: positions are in compressed coordinates
     int rc = check_params(p);
     if (rc) return rc;
     if (n_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
@@ -1312,7 +1370,7 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     if (stats)
         for (auto &e : ev) MT_CK(cudaEventCreate(&e));
     EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, true, stats ? ev : nullptr, launches,
-                   xfn, xctx};
+                   xfn, xctx, keep_in, !host_io};
     rc = enqueue_classify(ctx, s);
     if (rc) { dfree(ws, s); return rc; }
 
@@ -1338,8 +1396,17 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
                            uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
                            int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
                            mt_stats *stats) {
-    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, nullptr, nullptr, taxon, nloc,
-                         locs, genome_hits, abundance, stats);
+    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, nullptr, nullptr, nullptr,
+                         taxon, nloc, locs, genome_hits, abundance, stats);
+}
+
+extern "C" int mt_classify_masked(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                                  uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
+                                  const uint8_t *keep, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                                  uint64_t *genome_hits, double *abundance, mt_stats *stats) {
+    if (!keep) return MT_EINVAL;
+    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, nullptr, nullptr, keep, taxon,
+                         nloc, locs, genome_hits, abundance, stats);
 }
 
 extern "C" int mt_classify_sharded(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
@@ -1348,8 +1415,86 @@ extern "C" int mt_classify_sharded(const mt_index *ix, const uint8_t *reads, uin
                                    int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits,
                                    double *abundance, mt_stats *stats) {
     if (!allreduce) return MT_EINVAL;
-    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, allreduce, ctx, taxon, nloc,
-                         locs, genome_hits, abundance, stats);
+    return classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, allreduce, ctx, nullptr, taxon,
+                         nloc, locs, genome_hits, abundance, stats);
+}
+
+// ---- containment alone (stage 1): seed hits per genome and the kept-genome mask ------------------
+extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                              uint64_t n_reads, uint32_t max_occ, uint32_t cont_num, uint32_t cont_den,
+                              int device_ptrs, void *stream, uint64_t *genome_hits, uint8_t *keep) {
+    if (!ix || !offsets || (!reads && n_bases) || !genome_hits) return MT_EINVAL;
+    if (max_occ > MT_MAX_OCC_LIMIT || cont_den == 0) return MT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t G = ix->G;
+    const bool host_io = !device_ptrs;
+    uint64_t off0 = 0;
+    if (host_io && n_reads) {
+        off0 = offsets[0];
+        for (uint64_t r = 0; r < n_reads; r++)
+            if (offsets[r + 1] < offsets[r] || offsets[r + 1] > n_bases) return MT_EINVAL;
+    } else if (n_reads) {
+        MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaStreamSynchronize(s));
+    }
+    // workspace: counters | hits | mask | I/O block | host-buffer staging (reads, offsets)
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_ctr = 0, o_hits = up(sizeof(Counters)), o_keep = o_hits + up(G * 8ull);
+    const size_t o_io = o_keep + up(G), o_reads = o_io + up(sizeof(IoBlock));
+    const size_t o_off = o_reads + (host_io ? up(std::max<uint64_t>(n_bases, 1)) : 0);
+    const size_t total = o_off + (host_io ? up((n_reads + 1) * 8) : 0);
+    unsigned char *ws = nullptr;
+    int rc = dalloc((void **)&ws, total, s);
+    if (rc) return rc;
+    Counters *ctr = (Counters *)(ws + o_ctr);
+    unsigned long long *ghits = (unsigned long long *)(ws + o_hits);
+    uint8_t *dkeep = ws + o_keep;
+    auto fail = [&](int code) { dfree(ws, s); return code; };
+    if (cudaMemsetAsync(ws, 0, o_keep, s) != cudaSuccess) return fail(MT_ECUDA);
+    IoBlock hio{};
+    hio.reads = reads;
+    hio.roff = offsets;
+    hio.n_reads = n_reads;
+    hio.n_bases = n_bases;
+    hio.off0 = off0;
+    hio.max_len = MT_MAX_READ_LEN;
+    if (host_io) {
+        hio.reads = ws + o_reads;
+        hio.roff = (const uint64_t *)(ws + o_off);
+        if (n_bases && cudaMemcpyAsync((void *)hio.reads, reads, n_bases, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(MT_ECUDA);
+        if (cudaMemcpyAsync((void *)hio.roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(MT_ECUDA);
+    }
+    hio.vec_ok = ((uintptr_t)hio.reads & 15u) == 0;
+    if (cudaMemcpyAsync(ws + o_io, &hio, sizeof(hio), cudaMemcpyHostToDevice, s) != cudaSuccess) return fail(MT_ECUDA);
+    if (n_reads) {
+        SeedArgs A{};
+        A.ix = ix->view();
+        A.io = (const IoBlock *)(ws + o_io);
+        A.min_seeds = 1;
+        A.max_occ = max_occ;
+        A.ghits = ghits;
+        A.ctr = ctr;
+        const bool smem_hist = G <= SMEM_HIST_MAX;
+        const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem<uint64_t>);
+        const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
+        if (ix->hpc) rc = smem_hist ? launch_seed<true, false, true, true>(A, smem, need, s)
+                                    : launch_seed<false, false, true, true>(A, smem, need, s);
+        else rc = smem_hist ? launch_seed<true, false, true, false>(A, smem, need, s)
+                            : launch_seed<false, false, true, false>(A, smem, need, s);
+        if (rc) return fail(rc);
+    }
+    k_mask<<<1, 1024, 0, s>>>(ghits, G, cont_num, cont_den, dkeep);
+    if (!cuda_ok(cudaGetLastError(), "k_mask")) return fail(MT_ECUDA);
+    const cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(genome_hits, ghits, G * 8ull, kind, s) != cudaSuccess) return fail(MT_ECUDA);
+    if (keep && cudaMemcpyAsync(keep, dkeep, G, kind, s) != cudaSuccess) return fail(MT_ECUDA);
+    Counters h{};
+    if (cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MT_ECUDA);
+    dfree(ws, s);
+    MT_CK(cudaStreamSynchronize(s));
+    return status_of(h.err);
 }
 
 // ---- plans: preallocated workspace + captured CUDA graph ---------------------------------------------
@@ -1372,7 +1517,7 @@ extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, u
                               uint64_t max_bases, uint32_t max_read_len, mt_plan **out) {
     if (!out) return MT_EINVAL;
     *out = nullptr;
-    if (!ix || check_params(p) || max_reads == 0 || max_read_len == 0 || max_read_len > MT_MAX_READ_LEN)
+    if (!ix || ix->hpc || check_params(p) || max_reads == 0 || max_read_len == 0 || max_read_len > MT_MAX_READ_LEN)
         return MT_EINVAL;
     if (max_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
     const uint32_t maxE = edit_threshold(max_read_len, p->e_abs, p->e_permille);

@@ -233,6 +233,47 @@ __global__ void k_insert(const uint64_t *ucode, const uint32_t *ucount, const ui
     }
 }
 
+// ---- homopolymer compression (the containment index's seeds, minimap2's -H) ------------------
+// Each run of one repeated byte in a sequence becomes one byte; runs never join across
+// sequences. One block per sequence: count, then write in tiles of 4 bytes a thread with a
+// block-wide scan of the kept counts.
+static constexpr int HPC_THREADS = 256;
+
+__global__ void __launch_bounds__(HPC_THREADS) k_hpc_count(const uint8_t *seq, const uint64_t *off,
+                                                             uint64_t *cnt) {
+    const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+    uint64_t c = 0;
+    for (uint64_t j = a + threadIdx.x; j < b; j += HPC_THREADS) c += (j == a || seq[j] != seq[j - 1]);
+    typedef cub::BlockReduce<uint64_t, HPC_THREADS> Reduce;
+    __shared__ typename Reduce::TempStorage tmp;
+    const uint64_t tot = Reduce(tmp).Sum(c);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(HPC_THREADS) k_hpc_write(const uint8_t *seq, const uint64_t *off,
+                                                             const uint64_t *out_off, uint8_t *out) {
+    const uint64_t a = off[blockIdx.x], b = off[blockIdx.x + 1];
+    typedef cub::BlockScan<uint32_t, HPC_THREADS> Scan;
+    __shared__ typename Scan::TempStorage tmp;
+    uint64_t o = out_off[blockIdx.x];
+    for (uint64_t t0 = a; t0 < b; t0 += 4 * HPC_THREADS) {
+        const uint64_t j0 = t0 + 4ull * threadIdx.x;
+        uint32_t keep = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const uint64_t j = j0 + q;
+            if (j < b && (j == a || seq[j] != seq[j - 1])) keep |= 1u << q;
+        }
+        uint32_t pos, total;
+        Scan(tmp).ExclusiveSum((uint32_t)__popc(keep), pos, total);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (keep & (1u << q)) out[o + pos++] = seq[j0 + q];
+        o += total;
+        __syncthreads();   // tmp is reused by the next tile
+    }
+}
+
 }  // namespace mt
 
 using namespace mt;
@@ -246,10 +287,46 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t 
         if (offsets[g + 1] - offsets[g] >= (1ull << 32)) return MT_EINVAL;
     }
     ix->G = G; ix->k = p->k; ix->w = p->w; ix->canonical = p->canonical ? 1 : 0;
-    ix->total_bases = total;
-    ix->h_glen.resize(G);
+    ix->hpc = (p->flags & MT_INDEX_HPC) ? 1 : 0;
     std::vector<uint64_t> hoff(G + 1), hgword(G);
     for (uint32_t g = 0; g <= G; g++) hoff[g] = offsets[g] - off0;
+
+    int rc = MT_OK;
+    uint8_t *d_seq = nullptr;
+    uint64_t *d_off = nullptr;
+    uint32_t *d_err = nullptr;
+    uint32_t h_err = 0;
+    if ((rc = dalloc((void **)&d_seq, std::max<uint64_t>(total, 1), s))) return rc;
+    if ((rc = dalloc((void **)&d_off, (G + 1) * 8, s))) return rc;
+    if ((rc = dalloc((void **)&d_err, 4, s))) return rc;
+    if (total) MT_CK(cudaMemcpyAsync(d_seq, genomes + off0, total, cudaMemcpyHostToDevice, s));
+    MT_CK(cudaMemcpyAsync(d_off, hoff.data(), (G + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (ix->hpc) {   // the genomes are indexed in homopolymer-compressed form
+        uint64_t *d_cnt = nullptr, *d_off2 = nullptr;
+        uint8_t *d_seq2 = nullptr;
+        if ((rc = dalloc((void **)&d_cnt, G * 8ull, s))) return rc;
+        k_hpc_count<<<G, HPC_THREADS, 0, s>>>(d_seq, d_off, d_cnt);
+        MT_CK(cudaGetLastError());
+        std::vector<uint64_t> cnt(G);
+        MT_CK(cudaMemcpyAsync(cnt.data(), d_cnt, G * 8ull, cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaStreamSynchronize(s));
+        dfree(d_cnt, s);
+        std::vector<uint64_t> hoff2(G + 1, 0);
+        for (uint32_t g = 0; g < G; g++) hoff2[g + 1] = hoff2[g] + cnt[g];
+        if ((rc = dalloc((void **)&d_seq2, std::max<uint64_t>(hoff2[G], 1), s))) return rc;
+        if ((rc = dalloc((void **)&d_off2, (G + 1) * 8, s))) return rc;
+        MT_CK(cudaMemcpyAsync(d_off2, hoff2.data(), (G + 1) * 8, cudaMemcpyHostToDevice, s));
+        k_hpc_write<<<G, HPC_THREADS, 0, s>>>(d_seq, d_off, d_off2, d_seq2);
+        MT_CK(cudaGetLastError());
+        dfree(d_seq, s);
+        dfree(d_off, s);
+        d_seq = d_seq2;
+        d_off = d_off2;
+        hoff = hoff2;
+        total = hoff2[G];
+    }
+    ix->total_bases = total;
+    ix->h_glen.resize(G);
     for (uint32_t g = 0; g < G; g++) {
         ix->h_glen[g] = hoff[g + 1] - hoff[g];
         hgword[g] = (hoff[g] >> 5) + g;
@@ -264,16 +341,6 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t 
         ix->hk_db = (gb + 1 + db <= 32) ? db : 0;
     }
 
-    int rc = MT_OK;
-    uint8_t *d_seq = nullptr;
-    uint64_t *d_off = nullptr;
-    uint32_t *d_err = nullptr;
-    uint32_t h_err = 0;
-    if ((rc = dalloc((void **)&d_seq, total, s))) return rc;
-    if ((rc = dalloc((void **)&d_off, (G + 1) * 8, s))) return rc;
-    if ((rc = dalloc((void **)&d_err, 4, s))) return rc;
-    MT_CK(cudaMemcpyAsync(d_seq, genomes + off0, total, cudaMemcpyHostToDevice, s));
-    MT_CK(cudaMemcpyAsync(d_off, hoff.data(), (G + 1) * 8, cudaMemcpyHostToDevice, s));
     MT_CK(cudaMemsetAsync(d_err, 0, 4, s));
     MT_CK(cudaMalloc((void **)&ix->d_ref, ix->ref_words * 8));
     MT_CK(cudaMalloc((void **)&ix->d_gword, G * 8));
@@ -425,7 +492,7 @@ extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, u
     if (!out) return MT_EINVAL;
     *out = nullptr;
     if (!genomes || !offsets || !p || n_genomes == 0 || n_genomes > MT_MAX_GENOMES) return MT_EINVAL;
-    if (p->k < 1 || p->k > MT_MAX_K || p->w < 1 || p->w > MT_MAX_W || p->reserved != 0) return MT_EINVAL;
+    if (p->k < 1 || p->k > MT_MAX_K || p->w < 1 || p->w > MT_MAX_W || (p->flags & ~MT_INDEX_HPC) != 0) return MT_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     mt_index *ix = new mt_index();
     cudaGetDevice(&ix->device);
@@ -462,6 +529,8 @@ extern "C" int mt_index_get_info(const mt_index *ix, mt_index_info *info) {
     info->n_keys = ix->n_keys;
     info->table_slots = ix->slots;
     info->device_bytes = ix->device_bytes;
+    info->flags = ix->hpc ? MT_INDEX_HPC : 0u;
+    info->pad = 0;
     return MT_OK;
 }
 

@@ -3,7 +3,7 @@
 // onto a device without rebuilding.
 //
 // File layout (native little-endian): a 128-byte header
-//   "MTIDX\0\0\1" | u32 G, k, w, canonical, slot_shift, hk_db | u64 total_bases, n_occ,
+//   "MTIDX\0\0\1" | u32 G, k, w, canonical, slot_shift, hk_db, flags | u64 total_bases, n_occ,
 //   n_keys, slots, ref_words, occ_bytes | u64 check (FNV-1a of the preceding bytes) | zero pad
 // then the arrays glen[G], gword[G], ref[ref_words], table[slots] (32 bytes a slot),
 // occ[occ_bytes / 8], and the 8-byte trailer "MTIDXEND".
@@ -26,7 +26,7 @@ constexpr size_t STAGE_BYTES = 64ull << 20;
 
 struct Header {
     char magic[8];
-    uint32_t G, k, w, canonical, slot_shift, hk_db;
+    uint32_t G, k, w, canonical, slot_shift, hk_db, flags;
     uint64_t total_bases, n_occ, n_keys, slots, ref_words, occ_bytes;
     uint64_t check;
 };
@@ -78,7 +78,7 @@ bool header_ok(const Header &h) {
     if (memcmp(h.magic, MAGIC, 8) != 0) return false;
     if (h.check != fnv1a(&h, offsetof(Header, check))) return false;
     if (h.G == 0 || h.G > MT_MAX_GENOMES || h.k == 0 || h.k > MT_MAX_K || h.w == 0 || h.w > MT_MAX_W) return false;
-    if (h.canonical > 1 || h.slots == 0 || (h.slots & (h.slots - 1)) != 0) return false;
+    if (h.canonical > 1 || (h.flags & ~MT_INDEX_HPC) != 0 || h.slots == 0 || (h.slots & (h.slots - 1)) != 0) return false;
     uint32_t lg = 0;
     while ((1ull << lg) < h.slots) lg++;
     if (h.slot_shift != 64 - lg || h.n_keys > h.slots || h.n_keys > h.n_occ + 1) return false;
@@ -98,7 +98,7 @@ extern "C" int mt_save_index(const mt_index *ix, const char *path, void *stream)
     Header h{};
     memcpy(h.magic, MAGIC, 8);
     h.G = ix->G; h.k = ix->k; h.w = ix->w; h.canonical = ix->canonical;
-    h.slot_shift = ix->slot_shift; h.hk_db = ix->hk_db;
+    h.slot_shift = ix->slot_shift; h.hk_db = ix->hk_db; h.flags = ix->hpc ? MT_INDEX_HPC : 0u;
     h.total_bases = ix->total_bases; h.n_occ = ix->n_occ; h.n_keys = ix->n_keys; h.slots = ix->slots;
     h.ref_words = ix->ref_words;
     h.occ_bytes = std::max<uint64_t>(1, ix->n_occ) * 8;
@@ -143,7 +143,7 @@ extern "C" int mt_load_index(const char *path, void *stream, mt_index **out) {
 
     std::unique_ptr<mt_index, void (*)(mt_index *)> ix(new mt_index(), mt_free_index);
     ix->G = h.G; ix->k = h.k; ix->w = h.w; ix->canonical = h.canonical;
-    ix->slot_shift = h.slot_shift; ix->hk_db = h.hk_db;
+    ix->slot_shift = h.slot_shift; ix->hk_db = h.hk_db; ix->hpc = (h.flags & MT_INDEX_HPC) ? 1 : 0;
     ix->total_bases = h.total_bases; ix->n_occ = h.n_occ; ix->n_keys = h.n_keys; ix->slots = h.slots;
     ix->ref_words = h.ref_words;
     MT_CK(cudaGetDevice(&ix->device));

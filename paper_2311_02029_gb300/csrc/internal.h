@@ -46,6 +46,7 @@ struct mt_index {
     uint64_t total_bases = 0, n_occ = 0, n_keys = 0, slots = 0;
     uint32_t slot_shift = 0;
     uint32_t hk_db = 0;          // diagonal bits of 32-bit match keys; 0 if they do not fit
+    uint32_t hpc = 0;            // built over homopolymer-compressed genomes (containment only)
     uint64_t ref_words = 0;
     uint64_t *d_ref = nullptr, *d_gword = nullptr, *d_glen = nullptr, *d_occ = nullptr;
     ulonglong2 *d_table = nullptr;

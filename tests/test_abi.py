@@ -43,7 +43,7 @@ def test_struct_layouts_match_header(mtlib):
     assert ctypes.sizeof(mtlib.ClassifyParams) == 40
     assert mtlib.LOC_DTYPE.itemsize == 24
     assert ctypes.sizeof(mtlib.Stats) == 136
-    assert ctypes.sizeof(mtlib.IndexInfo) == 56
+    assert ctypes.sizeof(mtlib.IndexInfo) == 64
 
 
 def test_status_strings_and_argument_checks_without_gpu(mtlib):
