@@ -94,6 +94,7 @@ struct SeedArgs {
     unsigned long long *ghits;
     uint32_t *fb_list;
     Counters *ctr;
+    uint64_t r_begin, r_end;   // the reads this launch takes: [r_begin, min(r_end, n_reads))
 };
 
 // ---- read packing (one warp) ------------------------------------------------------------
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
 
     const IoBlock io = *A.io;
     const uint64_t total_warps = (uint64_t)gridDim.x * SEED_WARPS;
-    for (uint64_t r = (uint64_t)blockIdx.x * SEED_WARPS + warp; r < io.n_reads; r += total_warps) {
+    const uint64_t r_end = umin64(A.r_end, io.n_reads);
+    for (uint64_t r = A.r_begin + (uint64_t)blockIdx.x * SEED_WARPS + warp; r < r_end; r += total_warps) {
         const uint64_t start = io.roff[r], end = io.roff[r + 1];
         if (end < start || end > io.n_bases) {
             if (lane == 0) { atomicOr(&A.ctr->err, ERR_BAD_OFFSETS); if (!COUNT) A.qcnt[r] = 0; }
@@ -1117,6 +1119,11 @@ struct EnqueueCtx {
     void *xctx;
     const uint8_t *keep_in;   // a caller's genome mask replacing the containment mask, or null
     bool keep_dev;            // keep_in is a device pointer
+    // reads arriving in chunks (host buffers): chunk i holds reads [chunk_r[i], chunk_r[i+1])
+    // and is usable once chunk_ev[i] has fired; none: all reads are resident
+    uint32_t n_chunks;
+    const uint64_t *chunk_r;
+    const cudaEvent_t *chunk_ev;
 };
 
 // Replaces the G-vector at `dev` with its sum over the ranks of a sharded batch (a no-op for an
@@ -1176,9 +1183,23 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         const bool smem_hist = G <= SMEM_HIST_MAX;
         const bool hk32 = ix->hk_db != 0;
         const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * (hk32 ? sizeof(WarpSmem<uint32_t>) : sizeof(WarpSmem<uint64_t>));
-        const uint64_t need = (c.cap_reads + SEED_WARPS - 1) / SEED_WARPS;
-        int rc = hk32 ? (smem_hist ? launch_seed<true, true>(A, smem, need, s) : launch_seed<false, true>(A, smem, need, s))
-                      : (smem_hist ? launch_seed<true, false>(A, smem, need, s) : launch_seed<false, false>(A, smem, need, s));
+        auto seed = [&](uint64_t rb, uint64_t re) {
+            A.r_begin = rb;
+            A.r_end = re;
+            const uint64_t need = (std::min<uint64_t>(re, c.cap_reads) - rb + SEED_WARPS - 1) / SEED_WARPS;
+            return hk32 ? (smem_hist ? launch_seed<true, true>(A, smem, need, s) : launch_seed<false, true>(A, smem, need, s))
+                        : (smem_hist ? launch_seed<true, false>(A, smem, need, s) : launch_seed<false, false>(A, smem, need, s));
+        };
+        int rc = MT_OK;
+        if (c.n_chunks) {   // seed each chunk of reads as soon as its bytes have arrived
+            for (uint32_t i = 0; i < c.n_chunks && !rc; i++) {
+                MT_CK(cudaStreamWaitEvent(s, c.chunk_ev[i], 0));
+                rc = seed(c.chunk_r[i], c.chunk_r[i + 1]);
+            }
+            c.launches += c.n_chunks - 1;
+        } else {
+            rc = seed(0, ~0ull);
+        }
         if (rc) return rc;
         mark(1);
         if ((rc = exchange(c, s, ghits, G, MT_XCHG_GENOME_HITS))) return rc;
@@ -1311,38 +1332,40 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     const bool host_io = !device_ptrs;
     if (stats) memset(stats, 0, sizeof(*stats));
 
-    // longest read and offset checks
+    // longest read and offset checks, on the device (host offsets are copied there first)
     uint32_t maxn = 0;
     uint64_t off0 = 0, launches = 0;
-    if (host_io) {
-        if (n_reads) off0 = offsets[0];
-        for (uint64_t r = 0; r < n_reads; r++) {
-            if (offsets[r + 1] < offsets[r] || offsets[r + 1] > n_bases) return MT_EINVAL;
-            maxn = (uint32_t)std::max<uint64_t>(maxn, std::min<uint64_t>(offsets[r + 1] - offsets[r], 0xFFFFFFFFull));
+    uint64_t *d_roff = nullptr;   // host batches: the device copy of the offsets
+    if (n_reads) {
+        if (host_io) {
+            off0 = offsets[0];
+            if ((rc = dalloc((void **)&d_roff, (n_reads + 1) * 8, s))) return rc;
+            MT_CK(cudaMemcpyAsync(d_roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
         }
-    } else if (n_reads) {
         Counters *pre = nullptr;
         if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) return rc;
         MT_CK(cudaMemsetAsync(pre, 0, sizeof(Counters), s));
         unsigned blocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 4);
-        k_maxlen<<<blocks, 256, 0, s>>>(offsets, n_reads, n_bases, pre);
+        k_maxlen<<<blocks, 256, 0, s>>>(host_io ? d_roff : offsets, n_reads, n_bases, pre);
         MT_CK(cudaGetLastError());
         launches++;
         Counters h{};
         MT_CK(cudaMemcpyAsync(&h, pre, sizeof(h), cudaMemcpyDeviceToHost, s));
-        MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
+        if (!host_io) MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
         MT_CK(cudaStreamSynchronize(s));
         dfree(pre, s);
-        if (h.err) return MT_EINVAL;
+        if (h.err) { if (d_roff) dfree(d_roff, s); return MT_EINVAL; }
         maxn = h.maxn;
     }
-    if (maxn > MT_MAX_READ_LEN) return MT_EINVAL;
     const uint32_t maxE = edit_threshold(maxn, p->e_abs, p->e_permille);
-    if (maxE > MT_MAX_E) return MT_EINVAL;
+    if (maxn > MT_MAX_READ_LEN || maxE > MT_MAX_E) {
+        if (d_roff) dfree(d_roff, s);
+        return MT_EINVAL;
+    }
 
     Layout L = plan_layout(ix, n_bases, n_reads, top_n, std::max<uint32_t>(maxn, 1), p->max_occ, host_io);
     unsigned char *ws = nullptr;
-    if ((rc = dalloc((void **)&ws, L.total, s))) return rc;
+    if ((rc = dalloc((void **)&ws, L.total, s))) { if (d_roff) dfree(d_roff, s); return rc; }
     auto P = [&](size_t off) { return (void *)(ws + off); };
     IoBlock hio;
     hio.reads = reads;
@@ -1354,14 +1377,57 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     hio.taxon = taxon;
     hio.nloc = nloc;
     hio.locs = locs;
+    // Host reads go up in chunks on a second stream; the seeding of a chunk waits only for its
+    // own bytes, so the copy of the next chunk overlaps it.
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
+    std::vector<uint64_t> chunk_r;
+    auto release = [&]() {
+        for (auto e : chunk_ev) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+        if (d_roff) dfree(d_roff, s);
+    };
     if (host_io) {
         hio.reads = (const uint8_t *)P(L.reads);
-        hio.roff = (const uint64_t *)P(L.roff);
+        hio.roff = n_reads ? d_roff : (const uint64_t *)P(L.roff);
         hio.taxon = (int32_t *)P(L.taxon);
         hio.nloc = (uint8_t *)P(L.nloc);
         hio.locs = locs ? (mt_loc *)P(L.locs) : nullptr;
-        if (n_bases) MT_CK(cudaMemcpyAsync((void *)hio.reads, reads, n_bases, cudaMemcpyHostToDevice, s));
-        MT_CK(cudaMemcpyAsync((void *)hio.roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (!n_reads) MT_CK(cudaMemcpyAsync((void *)hio.roff, offsets, 8, cudaMemcpyHostToDevice, s));
+        const uint64_t span = n_reads ? offsets[n_reads] - off0 : 0;
+        const uint64_t chunk = std::max<uint64_t>(32ull << 20, span / 16);
+        if (span > chunk) {
+            int e_ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+            cudaEvent_t ready = nullptr;
+            e_ok = e_ok && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
+            if (ready) chunk_ev.push_back(ready);
+            // the copies follow the workspace allocation and the offsets, which are ordered on s
+            e_ok = e_ok && cudaEventRecord(ready, s) == cudaSuccess && cudaStreamWaitEvent(cs, ready, 0) == cudaSuccess;
+            chunk_r.push_back(0);
+            for (uint64_t rb = 0; e_ok && rb < n_reads;) {
+                const uint64_t limit = offsets[rb] + chunk;
+                uint64_t re = (uint64_t)(std::upper_bound(offsets + rb + 1, offsets + n_reads + 1, limit) - offsets) - 1;
+                if (re <= rb) re = rb + 1;
+                cudaEvent_t ev = nullptr;
+                e_ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+                if (ev) chunk_ev.push_back(ev);
+                const uint64_t b0 = offsets[rb], b1 = offsets[re];
+                if (e_ok && b1 > b0)
+                    e_ok = cudaMemcpyAsync((uint8_t *)hio.reads + b0, reads + b0, b1 - b0, cudaMemcpyHostToDevice, cs) == cudaSuccess;
+                e_ok = e_ok && cudaEventRecord(ev, cs) == cudaSuccess;
+                chunk_r.push_back(re);
+                rb = re;
+            }
+            if (!e_ok) {
+                cudaStreamSynchronize(cs);
+                release();
+                dfree(ws, s);
+                cuda_ok(cudaGetLastError(), "chunked read copies");
+                return MT_ECUDA;
+            }
+        } else if (n_bases) {
+            MT_CK(cudaMemcpyAsync((void *)hio.reads, reads, n_bases, cudaMemcpyHostToDevice, s));
+        }
     }
     hio.vec_ok = ((uintptr_t)hio.reads & 15u) == 0;
     MT_CK(cudaMemcpyAsync(P(L.io), &hio, sizeof(hio), cudaMemcpyHostToDevice, s));
@@ -1370,9 +1436,20 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     if (stats)
         for (auto &e : ev) MT_CK(cudaEventCreate(&e));
     EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, true, stats ? ev : nullptr, launches,
-                   xfn, xctx, keep_in, !host_io};
+                   xfn, xctx, keep_in, !host_io, 0, nullptr, nullptr};
+    if (cs) {
+        ctx.n_chunks = (uint32_t)(chunk_r.size() - 1);
+        ctx.chunk_r = chunk_r.data();
+        ctx.chunk_ev = chunk_ev.data() + 1;
+    }
     rc = enqueue_classify(ctx, s);
-    if (rc) { dfree(ws, s); return rc; }
+    if (rc) {
+        if (cs) cudaStreamSynchronize(cs);
+        dfree(ws, s);
+        cudaStreamSynchronize(s);
+        release();
+        return rc;
+    }
 
     cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (genome_hits) MT_CK(cudaMemcpyAsync(genome_hits, P(L.ghits), G * 8, kind, s));
@@ -1386,6 +1463,7 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     MT_CK(cudaMemcpyAsync(&h, P(L.ctr), sizeof(h), cudaMemcpyDeviceToHost, s));
     dfree(ws, s);
     MT_CK(cudaStreamSynchronize(s));
+    release();
     fill_stats(stats, h, n_reads, L.total, ctx.launches, stats ? ev : nullptr);
     if (stats)
         for (auto &e : ev) cudaEventDestroy(e);
@@ -1476,6 +1554,8 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
         A.max_occ = max_occ;
         A.ghits = ghits;
         A.ctr = ctr;
+        A.r_begin = 0;
+        A.r_end = ~0ull;
         const bool smem_hist = G <= SMEM_HIST_MAX;
         const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem<uint64_t>);
         const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;

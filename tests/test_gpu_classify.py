@@ -269,3 +269,33 @@ def test_empty_batch(mt, tiny):
     assert len(out["taxon"]) == 0
     assert out["genome_hits"].tolist() == [0] * g.n
     assert out["abundance"].tolist() == [0.0] * g.n
+
+
+def test_host_batch_uploaded_in_chunks(mt):
+    """A host batch above the 32 MB chunk size goes up in several chunks, each seeded as it
+    lands: results equal the device-buffer call's, read for read, and the oracle's on a sample."""
+    import torch
+    c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=500_000)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    assert len(r.seq) > (64 << 20) // 2
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    prm = _params(c, e_permille=0)
+    host = mt.classify(ix, r.seq, r.offsets, **prm)
+    dev = mt.classify(ix, torch.from_numpy(r.seq).cuda(), torch.from_numpy(r.offsets.astype(np.int64)).cuda(), **prm)
+    assert np.array_equal(host["taxon"], dev["taxon"].cpu().numpy())
+    assert np.array_equal(host["nloc"], dev["nloc"].cpu().numpy())
+    assert np.array_equal(host["locs"], mt.locs_from_device(dev["locs"]))
+    assert np.array_equal(host["genome_hits"], dev["genome_hits"].cpu().numpy().view(np.uint64))
+    # page-locked output buffers
+    def pinned(shape, dtype):
+        n = int(np.prod(shape)) * np.dtype(dtype).itemsize
+        return torch.empty(n, dtype=torch.uint8).pin_memory().numpy().view(dtype).reshape(shape)
+    pout = dict(taxon=pinned((r.n,), np.int32), nloc=pinned((r.n,), np.uint8), locs=pinned((r.n, 3), mt.LOC_DTYPE),
+                genome_hits=pinned((g.n,), np.uint64), abundance=pinned((g.n,), np.float64))
+    pres = mt.classify(ix, r.seq, r.offsets, out=pout, **prm)
+    for k in ("taxon", "nloc", "locs", "genome_hits", "abundance"):
+        assert np.array_equal(pres[k], host[k]), k
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=16)
+    compare_classify(host, ref)
