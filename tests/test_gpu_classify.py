@@ -239,6 +239,16 @@ def test_plan_graph_replays_match_oracle(mt, clade):
                               direct["taxon"])
     with pytest.raises(mt.MtError):
         plan.classify(r.seq, r.offsets)            # above the capacity
+    # inputs the kernels reject: a read above the plan's read length, offsets out of order
+    longer = np.concatenate([r.seq[:300], r.seq[:1]])
+    with pytest.raises(mt.MtError) as e:
+        plan.classify(longer, np.array([0, 149, 301], np.uint64))
+    assert e.value.status == mt.MT_EINVAL
+    with pytest.raises(mt.MtError) as e:
+        plan.classify(r.seq[:300], np.array([0, 200, 150, 300], np.uint64))
+    assert e.value.status == mt.MT_EINVAL
+    ok = plan.classify(r.seq[:300], np.array([0, 150, 300], np.uint64))   # still usable
+    assert len(ok["taxon"]) == 2
     plan.close()
 
 
