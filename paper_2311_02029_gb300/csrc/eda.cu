@@ -139,6 +139,8 @@ MT_DEV uint32_t approx(const uint64_t *rd, const uint64_t *wn, const PairInfo &p
     if (A == ALGO_QGRAM) return qgram_est<EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, reinterpret_cast<int *>(xb));
     if (A == ALGO_SHD)
         return shd_est<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl, reinterpret_cast<unsigned long long *>(xb));
+    if (G == 32 && (2 * pi.E + 1 + G - 1) / G <= SNAKE_TMAX)   // whole-warp groups: registers to spare
+        return sneaky_walk_cached<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl);
     return sneaky_walk<G, EDGES>(rd, wn, pi.n, pi.E, pi.lo, pi.hi, gmask, gl);
 }
 

@@ -39,6 +39,62 @@ MT_DEV uint32_t next_mismatch(const uint64_t *rd, const uint64_t *wn, uint32_t n
     return n;
 }
 
+// The walk when each lane has at most SNAKE_TMAX diagonals: the lanes keep 32-bit mismatch
+// masks of their diagonals over one 16-column block [B, B + 16) in registers, refilled when
+// the walk leaves the block, so a step inside the block costs a shift and a find-first-set a
+// diagonal. A run that reaches the block end continues with next_mismatch from B + 16. Same
+// result as the walk below.
+static constexpr uint32_t SNAKE_TMAX = 4;
+
+template <int G, bool EDGES>
+MT_DEV uint32_t sneaky_walk_cached(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E,
+                                   int32_t lo, int32_t hi, unsigned gmask, uint32_t glane) {
+    const uint32_t ndiag = 2 * E + 1;
+    const uint32_t T = (ndiag + G - 1) / G;
+    const uint32_t d0 = glane * T;
+    const uint32_t nt = d0 < ndiag ? min(T, ndiag - d0) : 0u;
+    uint32_t M[SNAKE_TMAX];
+    uint32_t c = 0, cnt = 0, B = 0;
+    bool fresh = false;
+    while (c < n) {
+        if (!fresh || c - B >= 16) {   // refill the masks at the current column
+            B = c;
+            fresh = true;
+            const uint32_t r0 = (uint32_t)get32(rd, B);
+            const uint64_t w0 = get32(wn, B + d0);
+            const uint64_t em = EDGES ? edge_mask((int32_t)(B + d0), lo, hi) : 0ull;
+#pragma unroll
+            for (uint32_t t = 0; t < SNAKE_TMAX; t++) {
+                if (t < nt) {
+                    const uint32_t y = r0 ^ (uint32_t)(w0 >> (2 * t));
+                    uint32_t m = (y | (y >> 1)) & 0x55555555u;
+                    if (EDGES) m |= (uint32_t)(em >> (2 * t)) & 0x55555555u;
+                    M[t] = m;
+                }
+            }
+        }
+        const uint32_t sh = 2 * (c - B);
+        uint32_t best = c;
+#pragma unroll
+        for (uint32_t t = 0; t < SNAKE_TMAX; t++) {
+            if (t < nt) {
+                const uint32_t r = M[t] >> sh;
+                uint32_t e = r ? c + ((uint32_t)(__ffs((int)r) - 1) >> 1)
+                               : next_mismatch<EDGES>(rd, wn, n, B + 16, d0 + t, lo, hi);
+                e = e < n ? e : n;
+                best = e > best ? e : best;
+            }
+        }
+        if (G > 1) best = __reduce_max_sync(gmask, best);
+        c = best;
+        if (c >= n) break;
+        cnt++;
+        if (cnt > E) break;
+        c++;
+    }
+    return cnt < E + 1 ? cnt : E + 1;
+}
+
 // The walk for one pair, executed by the G lanes of `gmask` (glane = lane within group).
 // Lane glane owns the contiguous diagonal range [glane*T, glane*T + T), T = ceil((2E+1)/G).
 // Per step it loads the read's 32 columns from c once and the window's bases from c + its
