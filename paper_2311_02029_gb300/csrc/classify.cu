@@ -677,7 +677,9 @@ __global__ void k_mask(const unsigned long long *hits, uint32_t G, uint32_t num,
 __global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep,
                          uint32_t top_n, Cluster *cand, uint8_t *nloc_ws, uint32_t *cl, uint32_t *fb_list,
                          Counters *ctr) {
-    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_base;
     const uint64_t n_reads = io->n_reads;
     for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t r = r0 + threadIdx.x;
@@ -702,13 +704,23 @@ __global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster 
             unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->fb_count), 1ull);
             fb_list[slot] = (uint32_t)r;
         }
-        // compact candidate slots
-        uint32_t incl = warp_incl_scan(taken);
-        uint32_t tot = __shfl_sync(FULL, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 31 && tot) base = atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->cl_count), (unsigned long long)tot);
-        base = __shfl_sync(FULL, base, 31);
+        // compact candidate slots: one counter update per block and tile
+        const uint32_t incl = warp_incl_scan(taken);
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (uint32_t i = 0; i < blockDim.x / 32; i++) {
+                const uint32_t t = s_warp[i];
+                s_warp[i] = run;
+                run += t;
+            }
+            s_base = run ? atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->cl_count), (unsigned long long)run) : 0;
+        }
+        __syncthreads();
+        const unsigned long long base = s_base + s_warp[warp];
         for (uint32_t t = 0; t < taken; t++) cl[base + incl - taken + t] = (uint32_t)(r * top_n + t);
+        __syncthreads();   // s_warp and s_base are reused by the next tile
     }
 }
 
@@ -863,21 +875,46 @@ struct DecideArgs {
     int32_t *multi_set;
     uint32_t *multi_list;
     Counters *ctr;
+    uint32_t G;
+    uint32_t hist;   // 1: unique counts are gathered per block in shared memory first
 };
 
-__global__ void k_decide(DecideArgs A) {
+// A block takes tiles of DECIDE_THREADS consecutive reads: their candidate records, distances
+// and location counts come into shared memory with contiguous loads, a thread decides its read
+// from there, and the location records go out as contiguous 8-byte words.
+static constexpr int DECIDE_THREADS = 256;
+
+__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const uint32_t tn = A.top_n;
+    // unique counts of the block (G counters), flushed once at the end
+    unsigned long long *s_U = reinterpret_cast<unsigned long long *>(dsm);
+    const uint32_t hist_n = A.hist ? A.G : 0;
+    for (uint32_t g = threadIdx.x; g < hist_n; g += DECIDE_THREADS) s_U[g] = 0;
+    unsigned long long *U = A.hist ? s_U : A.U;
+    Cluster *s_cand = reinterpret_cast<Cluster *>(dsm + (((size_t)hist_n * 8 + 15) & ~(size_t)15));   // DECIDE_THREADS * tn
+    uint64_t *s_locs = reinterpret_cast<uint64_t *>(s_cand + DECIDE_THREADS * tn);  // 3 words a location
+    uint8_t *s_dist = reinterpret_cast<uint8_t *>(s_locs + 3 * DECIDE_THREADS * tn);
+    uint8_t *s_nloc = s_dist + DECIDE_THREADS * tn;
     const uint32_t lane = threadIdx.x & 31u;
     unsigned long long acc = 0, mul = 0, cand = 0;
     const IoBlock io = *A.io;
-    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < io.n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t r0 = (uint64_t)blockIdx.x * DECIDE_THREADS; r0 < io.n_reads; r0 += (uint64_t)gridDim.x * DECIDE_THREADS) {
+        const uint32_t nr = (uint32_t)umin64(DECIDE_THREADS, io.n_reads - r0);
+        __syncthreads();   // the previous tile's locations are out
+        for (uint32_t i = threadIdx.x; i < nr * tn; i += DECIDE_THREADS) {
+            s_cand[i] = A.cand[r0 * tn + i];
+            s_dist[i] = A.dist[r0 * tn + i];
+        }
+        if (threadIdx.x < nr) s_nloc[threadIdx.x] = A.nloc_ws[r0 + threadIdx.x];
+        __syncthreads();
         const uint64_t r = r0 + threadIdx.x;
         int32_t uniq = -1;
         bool is_multi = false;
-        if (r < io.n_reads) {
+        if (threadIdx.x < nr) {
             const uint32_t n = (uint32_t)(io.roff[r + 1] - io.roff[r]);
             const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
-            const uint32_t nl = A.nloc_ws[r];
-            const uint32_t tn = A.top_n;
+            const uint32_t nl = s_nloc[threadIdx.x];
             cand += nl;
             // every loop below runs over the at most MT_MAX_TOPN slots with static indices
             uint32_t d[MT_MAX_TOPN];
@@ -888,8 +925,8 @@ __global__ void k_decide(DecideArgs A) {
                 d[t] = 0xFFu;
                 cl[t].hkey = 0; cl[t].seeds = 0; cl[t].pad = 0;
                 if (t < nl) {
-                    d[t] = A.dist[r * tn + t];
-                    cl[t] = A.cand[r * tn + t];
+                    d[t] = s_dist[threadIdx.x * tn + t];
+                    cl[t] = s_cand[threadIdx.x * tn + t];
                     if (d[t] <= E && d[t] < best) best = d[t];
                 }
             }
@@ -921,7 +958,7 @@ __global__ void k_decide(DecideArgs A) {
                         L.strand = (uint8_t)hk_rel(cl[t].hkey);
                         L.dist = (uint8_t)d[t];
                     }
-                    io.locs[r * tn + t] = L;
+                    memcpy(&s_locs[3 * (threadIdx.x * tn + t)], &L, sizeof(L));
                 }
             }
             io.taxon[r] = tax;
@@ -945,13 +982,18 @@ __global__ void k_decide(DecideArgs A) {
         unsigned act = __ballot_sync(FULL, uniq >= 0);
         if (uniq >= 0) {
             unsigned peers = __match_any_sync(act, uniq);
-            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&A.U[uniq], (unsigned long long)__popc(peers));
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&U[uniq], (unsigned long long)__popc(peers));
         }
         unsigned mb = __ballot_sync(FULL, is_multi);
         unsigned long long base = 0;
         if (lane == 0 && mb) base = atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctr->multi_count), (unsigned long long)__popc(mb));
         base = __shfl_sync(FULL, base, 0);
         if (is_multi) A.multi_list[base + __popc(mb & ((1u << lane) - 1u))] = (uint32_t)r;
+        if (io.locs) {
+            __syncthreads();
+            uint64_t *dst = reinterpret_cast<uint64_t *>(io.locs + r0 * tn);
+            for (uint32_t i = threadIdx.x; i < 3 * nr * tn; i += DECIDE_THREADS) dst[i] = s_locs[i];
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         acc += __shfl_xor_sync(FULL, acc, o);
@@ -962,6 +1004,11 @@ __global__ void k_decide(DecideArgs A) {
         atomicAdd(&A.ctr->stat[ST_ACC], acc);
         atomicAdd(&A.ctr->stat[ST_MULTI], mul);
         atomicAdd(&A.ctr->stat[ST_CAND], cand);
+    }
+    if (A.hist) {
+        __syncthreads();
+        for (uint32_t g = threadIdx.x; g < hist_n; g += DECIDE_THREADS)
+            if (s_U[g]) atomicAdd(&A.U[g], s_U[g]);
     }
 }
 
@@ -1248,7 +1295,18 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         D.multi_set = (int32_t *)P(L.multi_set);
         D.multi_list = (uint32_t *)P(L.multi_list);
         D.ctr = ctr;
-        k_decide<<<rblocks, 256, 0, s>>>(D);
+        {
+            static_assert(sizeof(mt_loc) == 24, "a location is three 8-byte words");
+            D.G = G;
+            D.hist = G <= SMEM_HIST_MAX;
+            const size_t dsmem = (D.hist ? (((size_t)G * 8 + 15) & ~(size_t)15) : 0) +
+                                 (size_t)DECIDE_THREADS * top_n * (sizeof(Cluster) + sizeof(mt_loc) + 1) + DECIDE_THREADS;
+            const unsigned dblocks = (unsigned)std::min<uint64_t>((c.cap_reads + DECIDE_THREADS - 1) / DECIDE_THREADS,
+                                                                  (uint64_t)sm_count() * 8);
+            if (dsmem > 48 * 1024)
+                MT_CK(cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+            k_decide<<<dblocks, DECIDE_THREADS, dsmem, s>>>(D);
+        }
         MT_CK(cudaGetLastError());
         if ((rc = exchange(c, s, U, G, MT_XCHG_UNIQUE))) return rc;
         k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(D.multi_list, ctr, D.multi_set, top_n, U, M);
