@@ -34,7 +34,7 @@ METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact)
 # kernel on 2e6 reads of the same workload (dram__bytes_read.sum + dram__bytes_write.sum); the
 # index is fixed, so traffic grows in proportion to the reads. None whenever the kernel has
 # changed since the last capture.
-SEED_DRAM_BYTES_PER_READ = (7.317347e9 + 0.250506e9) / 2e6
+SEED_DRAM_BYTES_PER_READ = (7.053661e9 + 0.250544e9) / 2e6
 WORKLOAD = ("medium: 200 genomes x 2 Mb (20 clades x 10, 1-10% divergence), k21 w11 canonical, "
             "1e7 reads x 150 bp (both strands, 0.5% subst + 0.05% indel, 5% random), E=8, min_seeds 3, top 3")
 

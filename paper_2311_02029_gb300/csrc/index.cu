@@ -452,8 +452,14 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t 
         dfree(d_tmp, s);
     }
 
+    // load factor <= 1/4 while the table stays within 16 GB (fewer warps wait on a second
+    // probe), else <= 1/2
     uint64_t slots = 1024;
-    while (slots < 2 * (uint64_t)n_keys) slots <<= 1;
+    while (slots < 4 * (uint64_t)n_keys) slots <<= 1;
+    if (slots * 32 > (16ull << 30)) {
+        slots = 1024;
+        while (slots < 2 * (uint64_t)n_keys) slots <<= 1;
+    }
     uint32_t lg = 0;
     while ((1ull << lg) < slots) lg++;
     ix->slots = slots;
