@@ -11,7 +11,9 @@ window minima, brute-force seed enumeration per genome, a hand-worked SneakySnak
 the E = 0 Hamming reduction, an exact dynamic-programming restatement of the greedy walk,
 upper bounds by per-diagonal Hamming distance and by banded edit distance (no false
 reject), a lower bound by all-obstacle columns, planted-truth mapping of error-free reads,
-and hand-computed abundance splits. Parity unpinned (defined readings with no external
+and hand-computed abundance splits; for a database cut into batches, reduction to the
+single-index pipeline when no key reaches the repeat filter, highest-not-summed counts of a
+genome held by several batches, and brute-force per-batch repeat filtering. Parity unpinned (defined readings with no external
 check): the location clustering rule, rank tie-breaks, the max_occ repeat filter and the
 multi-read split -- the CUDA path must still agree with them bit-exactly.
 """
@@ -284,6 +286,74 @@ def classify(ix: Index, reads_seq, reads_off, p: dict, threads: int = 1, keep=No
     a = abundance(m["U"], m["multi"], p["top_n"], p["abund_cutoff"])
     m.update(genome_hits=hits, keep=keep, abundance=a)
     return m
+
+
+def gather_genomes(genomes_seq, genomes_off, ids):
+    """The bytes and offsets of the genomes ``ids`` (in that order), concatenated."""
+    seq = _u8(genomes_seq)
+    off = np.asarray(genomes_off, dtype=np.uint64)
+    ids = np.asarray(ids, dtype=np.int64)
+    parts = [seq[int(off[g]):int(off[g + 1])] for g in ids]
+    out_off = np.zeros(len(ids) + 1, np.uint64)
+    out_off[1:] = np.cumsum([len(x) for x in parts]) if len(parts) else []
+    return (np.concatenate(parts) if parts else np.zeros(0, np.uint8)), out_off
+
+
+def partitioned_hits(batches, n_genomes: int, reads_seq, reads_off, max_occ: int, threads: int = 1):
+    """Stage 1 over a database cut into batches (Methods, "Reference Database Organisation
+    and Index Construction & Querying"): every batch is its own index, queried on its own,
+    so its repeat filter counts occurrences within that batch only; its seed hits are counted
+    per genome and mapped to global genome ids, and a genome held by several batches keeps
+    its highest count. ``batches``: a list of (Index, global ids of its genomes)."""
+    H = np.zeros(n_genomes, np.uint64)
+    for ix, ids in batches:
+        ids = np.asarray(ids, dtype=np.int64)
+        h = count_hits_sharded(ix, reads_seq, reads_off, max_occ, threads)
+        for l, g in enumerate(ids):
+            H[g] = max(H[g], h[l])
+    return H
+
+
+def classify_partitioned(batches, n_genomes: int, genomes_seq, genomes_off, reads_seq, reads_off, p: dict,
+                         k: int, w: int, canonical: int, threads: int = 1):
+    """The pipeline over a partitioned database, in the paper's order (Fig. 1; Methods,
+    "Reference Database Organisation and Index Construction & Querying"; Evaluation
+    Methodology):
+      1. seed hits per genome from every batch's own index, highest count per genome
+         (``partitioned_hits``);
+      2. the normalised cutoff over the whole database: keep g iff hits[g]/max > num/den;
+      3. the subset database: a new (k, w) index over the kept genomes only, in global id
+         order (``genomes_seq`` / ``genomes_off`` hold every genome, by global id);
+      4. read mapping and profiling against the subset, all of whose genomes are kept;
+         genome ids are reported as global ids.
+    With nothing kept, no read maps and every abundance is 0."""
+    s = _u8(reads_seq)
+    off = np.ascontiguousarray(reads_off, dtype=np.uint64)
+    n = len(off) - 1
+    tn = p["top_n"]
+    H = partitioned_hits(batches, n_genomes, s, off, p["max_occ"], threads)
+    keep = keep_mask(H, p["cont_num"], p["cont_den"])
+    kept = np.flatnonzero(keep)
+    if len(kept) == 0:
+        locs = np.zeros((n, tn), LOC_DTYPE)
+        locs["genome"] = -1
+        return dict(taxon=np.full(n, -1, np.int32), locs=locs, nloc=np.zeros(n, np.uint8),
+                    multi=np.full((n, tn), -1, np.int32), U=np.zeros(n_genomes, np.uint64),
+                    genome_hits=H, keep=keep, abundance=np.zeros(n_genomes), kept=kept)
+    sub_seq, sub_off = gather_genomes(genomes_seq, genomes_off, kept)
+    sub = Index(sub_seq, sub_off, k, w, canonical, threads=threads)
+    m = classify(sub, s, off, p, threads=threads, keep=np.ones(len(kept), np.uint8))
+    to_global = np.concatenate([kept.astype(np.int32), np.array([-1], np.int32)])
+    taxon = to_global[m["taxon"]]          # -1 indexes the trailing -1
+    locs = m["locs"].copy()
+    locs["genome"] = to_global[locs["genome"]]
+    multi = to_global[m["multi"]]
+    U = np.zeros(n_genomes, np.uint64)
+    U[kept] = m["U"]
+    a = np.zeros(n_genomes, np.float64)
+    a[kept] = m["abundance"]
+    return dict(taxon=taxon, locs=locs, nloc=m["nloc"], multi=multi, U=U, genome_hits=H, keep=keep,
+                abundance=a, kept=kept)
 
 
 def map_subset(ix: Index, reads_seq, reads_off, idx, p: dict, keep: np.ndarray, threads: int = 1):
