@@ -227,6 +227,70 @@ int mt_classify_masked(const mt_index *ix, const uint8_t *reads, uint64_t n_base
                        int device_ptrs, void *stream, const uint8_t *keep, int32_t *taxon, uint8_t *nloc,
                        mt_loc *locs, uint64_t *genome_hits, double *abundance, mt_stats *stats);
 
+/* ---- a reference database cut into batches (Methods, "Reference Database Organisation and
+ * Index Construction & Querying"; Evaluation Methodology) --------------------------------------
+ * The database is split into batches, each indexed on its own (built, saved, loaded and, when
+ * one of its genomes changes, rebuilt without touching the others); a batch's genomes carry
+ * global ids 0..n_genomes-1, and one genome may sit in several batches. One read batch is
+ * classified against it in the paper's order:
+ *  1. mt_part_contain, once per database batch: that batch's seed hits per genome over all the
+ *     reads, with the batch's own repeat filter (max_occ counts occurrences in that batch); a
+ *     genome keeps the highest count any batch gave it;
+ *  2. mt_part_subset: the normalised cutoff over the whole database, keep[g] =
+ *     (hits[g] * cont_den > max_h hits[h] * cont_num), and the list of kept genomes;
+ *  3. the caller builds the subset database, an index over the kept genomes in that order
+ *     (mt_build_index, any k / w, not MT_INDEX_HPC);
+ *  4. mt_part_classify: read mapping and profiling (stages 2 and 3 of mt_classify) against the
+ *     subset, all of whose genomes are kept; genome ids in the outputs are global ids.
+ * Only the reads and a few n_genomes vectors stay on the device between the calls, so the
+ * database batches can be loaded (mt_load_index), queried and freed one at a time: the
+ * database need not fit in device memory, only one batch and the subset index.
+ * All calls of a query run on its stream and return after synchronising it. */
+typedef struct mt_part mt_part;   /* opaque: one read batch queried against a partitioned database */
+
+/* Starts a query. reads / offsets / device_ptrs as in mt_classify; host inputs are copied to
+ * the device here (the caller's buffers are free on return); device inputs are borrowed until
+ * mt_part_destroy. n_genomes: global genome ids of the database, >= 1.
+ * Errors: MT_EINVAL (NULL arguments, n_genomes 0), MT_ENOMEM, MT_ECUDA. */
+int mt_part_create(uint32_t n_genomes, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                   uint64_t n_reads, int device_ptrs, void *stream, mt_part **out);
+/* Stage 1 for one database batch: genome_ids (host, batch's n_genomes entries, each <
+ * n_genomes) are the global ids of the batch's genomes in index order. Any index kind,
+ * including MT_INDEX_HPC (the paper's containment index).
+ * Errors: MT_EINVAL (NULL arguments, an id out of range, max_occ above MT_MAX_OCC_LIMIT, bad
+ * reads or offsets), MT_ENOMEM, MT_ECUDA. */
+int mt_part_contain(mt_part *q, const mt_index *batch, const uint32_t *genome_ids, uint32_t max_occ);
+/* The cutoff over the counts gathered so far. Outputs (each may be NULL): keep[n_genomes] (host),
+ * genome_hits[n_genomes] (the highest counts; host or device like the reads), kept (host,
+ * n_genomes entries of room: the kept global ids, increasing) and *n_kept.
+ * Errors: MT_EINVAL (NULL q, cont_den 0), MT_ECUDA. */
+int mt_part_subset(mt_part *q, uint32_t cont_num, uint32_t cont_den, uint8_t *keep, uint64_t *genome_hits,
+                   uint32_t *kept, uint32_t *n_kept);
+/* Stages 2 and 3 against the subset index: subset_ids (host, n_subset entries) must be the kept
+ * list of the last mt_part_subset, and subset an index over exactly those genomes in that
+ * order (NULL when n_subset is 0: then no read maps). params as in mt_classify (cont_num /
+ * cont_den unused). Outputs as in mt_classify, in global ids; abundance has n_genomes entries
+ * (0 for genomes not kept); genome_hits is reported by mt_part_subset instead.
+ * Errors: MT_EINVAL (mt_part_subset not called, a subset list or index that does not match
+ * it, an MT_INDEX_HPC subset, bad params), MT_ENOMEM, MT_ECUDA. */
+int mt_part_classify(mt_part *q, const mt_index *subset, const uint32_t *subset_ids, uint32_t n_subset,
+                     const mt_classify_params *params, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                     double *abundance, mt_stats *stats);
+void mt_part_destroy(mt_part *q);
+
+/* The four steps in one call over resident database batches: batches[b] with global ids
+ * genome_ids[b] (host arrays of each batch's n_genomes entries); genomes / genome_offsets (host,
+ * n_genomes + 1 offsets) hold every genome by global id, for the subset index, which is built
+ * with subset_params and freed before returning. Stage 1 uses params->max_occ and the cutoff
+ * params->cont_num / cont_den. Outputs as in mt_classify (genome_hits: the highest counts).
+ * Errors: those of the calls above and of mt_build_index. */
+int mt_classify_partitioned(const mt_index *const *batches, const uint32_t *const *genome_ids, uint32_t n_batches,
+                            const uint8_t *genomes, const uint64_t *genome_offsets, uint32_t n_genomes,
+                            const mt_index_params *subset_params, const uint8_t *reads, uint64_t n_bases,
+                            const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
+                            int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                            uint64_t *genome_hits, double *abundance, mt_stats *stats);
+
 /* ---- one batch sharded over several processes (ranks) -------------------------------------
  * Stages 1 and 3 are defined over the whole batch: the containment cutoff compares a genome's
  * hits with the largest hit count of the batch ("The MetaTrinity Pipeline", stage 1), and a

@@ -85,7 +85,8 @@ EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", 
            "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_containment", "mt_classify_masked", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
-           "mt_server_cancel", "mt_server_destroy"]
+           "mt_server_cancel", "mt_server_destroy", "mt_part_create", "mt_part_contain", "mt_part_subset",
+           "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned"]
 
 
 def lib():
@@ -147,6 +148,20 @@ def lib():
         L.mt_server_cancel.restype = i32
         L.mt_server_cancel.argtypes = [vp, u64]
         L.mt_server_destroy.argtypes = [vp]
+        L.mt_part_create.restype = i32
+        L.mt_part_create.argtypes = [u32, vp, u64, vp, u64, i32, vp, ctypes.POINTER(vp)]
+        L.mt_part_contain.restype = i32
+        L.mt_part_contain.argtypes = [vp, vp, vp, u32]
+        L.mt_part_subset.restype = i32
+        L.mt_part_subset.argtypes = [vp, u32, u32, vp, vp, vp, ctypes.POINTER(u32)]
+        L.mt_part_classify.restype = i32
+        L.mt_part_classify.argtypes = [vp, vp, vp, u32, ctypes.POINTER(ClassifyParams), vp, vp, vp, vp,
+                                       ctypes.POINTER(Stats)]
+        L.mt_part_destroy.argtypes = [vp]
+        L.mt_classify_partitioned.restype = i32
+        L.mt_classify_partitioned.argtypes = [vp, vp, u32, vp, vp, u32, ctypes.POINTER(IndexParams), vp, u64, vp,
+                                              u64, ctypes.POINTER(ClassifyParams), i32, vp, vp, vp, vp, vp, vp,
+                                              ctypes.POINTER(Stats)]
         _lib = L
     return _lib
 
@@ -381,6 +396,157 @@ def classify_sharded(ix: Index, reads, offsets, allreduce, *, stream=None, want_
     whole batch's."""
     cb = allreduce_callback(allreduce)
     return _classify(ix, reads, offsets, cb, stream, want_locs, out, params)
+
+
+# ---- a reference database cut into batches ------------------------------------------------------
+def split_batches(genome_offsets, n_batches: int) -> list:
+    """Global genome ids cut into ``n_batches`` runs of consecutive ids holding about equal
+    numbers of bases (the paper splits its database into batches of about 7 GB each); every
+    batch holds at least one genome."""
+    off = _host_u64(genome_offsets).astype(np.float64)
+    G = len(off) - 1
+    if not 1 <= n_batches <= G:
+        raise ValueError("n_batches must be in 1..n_genomes")
+    total = off[-1] - off[0]
+    cuts = [0]
+    for b in range(1, n_batches):
+        # the batch ends after the first genome whose end reaches b / n_batches of the bases
+        j = int(np.searchsorted(off[1:], off[0] + total * b / n_batches, side="left")) + 1
+        cuts.append(min(max(j, cuts[-1] + 1), G - (n_batches - b)))
+    cuts.append(G)
+    return [np.arange(cuts[i], cuts[i + 1], dtype=np.uint32) for i in range(n_batches)]
+
+
+def gather_genomes(genomes, genome_offsets, ids):
+    """Host bytes and offsets of the genomes ``ids``, concatenated in that order (the input of
+    a batch's or a subset's ``Index``)."""
+    g, off = _host_u8(genomes), _host_u64(genome_offsets)
+    ids = np.asarray(ids, dtype=np.int64)
+    lens = (off[ids + 1] - off[ids]).astype(np.uint64) if len(ids) else np.zeros(0, np.uint64)
+    out_off = np.zeros(len(ids) + 1, np.uint64)
+    out_off[1:] = np.cumsum(lens)
+    out = np.empty(max(int(out_off[-1]), 1), np.uint8)
+    for i, gid in enumerate(ids):
+        out[int(out_off[i]):int(out_off[i + 1])] = g[int(off[gid]):int(off[gid + 1])]
+    return out[:int(out_off[-1])], out_off
+
+
+def _part_outputs(dev, n_reads, top_n, G, want_locs):
+    if dev is not None:
+        import torch
+        return dict(taxon=torch.empty(n_reads, dtype=torch.int32, device=dev),
+                    nloc=torch.empty(n_reads, dtype=torch.uint8, device=dev),
+                    locs=torch.empty((n_reads, top_n, 24), dtype=torch.uint8, device=dev) if want_locs else None,
+                    genome_hits=torch.empty(G, dtype=torch.int64, device=dev),
+                    abundance=torch.empty(G, dtype=torch.float64, device=dev))
+    return dict(taxon=np.empty(n_reads, np.int32), nloc=np.empty(n_reads, np.uint8),
+                locs=np.empty((n_reads, top_n), LOC_DTYPE) if want_locs else None,
+                genome_hits=np.empty(G, np.uint64), abundance=np.empty(G, np.float64))
+
+
+class PartitionedQuery:
+    """``mt_part_*``: one read batch queried against a database cut into batches. Call
+    ``contain`` once per database batch (an Index and the global ids of its genomes), then
+    ``subset`` (the cutoff; returns the kept ids), build an Index over the kept genomes in
+    that order, and ``classify`` against it. Reads are host arrays or CUDA tensors (then kept
+    referenced until ``close``)."""
+
+    def __init__(self, n_genomes: int, reads, offsets, stream=None):
+        self.n_genomes = int(n_genomes)
+        self._stream = stream
+        self._dev = reads.device if (_is_torch(reads) and reads.is_cuda) else None
+        h = ctypes.c_void_p()
+        if self._dev is not None:
+            self._keep = (reads, offsets)
+            self.n_reads = offsets.numel() - 1
+            rc = lib().mt_part_create(self.n_genomes, _ptr(reads), reads.numel(), _ptr(offsets), self.n_reads, 1,
+                                      _stream(stream), ctypes.byref(h))
+        else:
+            r, off = _host_u8(reads), _host_u64(offsets)
+            self.n_reads = len(off) - 1
+            rc = lib().mt_part_create(self.n_genomes, _ptr(r), len(r), _ptr(off), self.n_reads, 0,
+                                      _stream(stream), ctypes.byref(h))
+        _check(rc, "mt_part_create")
+        self._h = h
+        self.kept = None
+
+    def contain(self, batch: Index, genome_ids, max_occ: int = 1024):
+        ids = np.ascontiguousarray(genome_ids, dtype=np.uint32)
+        if len(ids) != batch.n_genomes:
+            raise ValueError("one global id per genome of the batch")
+        _check(lib().mt_part_contain(self._h, batch.handle, _ptr(ids), max_occ), "mt_part_contain")
+
+    def subset(self, cont_num: int = 1, cont_den: int = 10000) -> dict:
+        G = self.n_genomes
+        keep = np.empty(G, np.uint8)
+        kept = np.empty(G, np.uint32)
+        nk = ctypes.c_uint32()
+        hits = _part_outputs(self._dev, 0, 1, G, False)["genome_hits"]
+        _check(lib().mt_part_subset(self._h, cont_num, cont_den, _ptr(keep), _ptr(hits), _ptr(kept), ctypes.byref(nk)),
+               "mt_part_subset")
+        self.kept = kept[:nk.value].copy()
+        return dict(keep=keep, genome_hits=hits, kept=self.kept)
+
+    def classify(self, subset: Index | None, *, want_locs=True, **params) -> dict:
+        p = classify_params(**params)
+        st = Stats()
+        ids = self.kept if self.kept is not None else np.zeros(0, np.uint32)
+        out = _part_outputs(self._dev, self.n_reads, p.top_n, self.n_genomes, want_locs)
+        del out["genome_hits"]
+        _check(lib().mt_part_classify(self._h, subset.handle if subset is not None else None, _ptr(ids), len(ids),
+                                      ctypes.byref(p), _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                      _ptr(out["abundance"]), ctypes.byref(st)), "mt_part_classify")
+        out["stats"] = st.as_dict()
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mt_part_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def classify_partitioned(batches, genome_ids, genomes, genome_offsets, reads, offsets, *, k: int, w: int,
+                         canonical: int = 1, stream=None, want_locs=True, **params) -> dict:
+    """``mt_classify_partitioned``: the whole query over resident database batches
+    (``batches[b]`` an Index whose genomes have global ids ``genome_ids[b]``); ``genomes`` /
+    ``genome_offsets`` (host) hold every genome by global id, for the subset index (k, w,
+    canonical)."""
+    if len(batches) != len(genome_ids):
+        raise ValueError("one id list per batch")
+    ids = [np.ascontiguousarray(x, dtype=np.uint32) for x in genome_ids]
+    for ix, x in zip(batches, ids):
+        if len(x) != ix.n_genomes:
+            raise ValueError("one global id per genome of each batch")
+    B = len(batches)
+    hv = (ctypes.c_void_p * max(B, 1))(*[ix.handle.value for ix in batches])
+    iv = (ctypes.c_void_p * max(B, 1))(*[x.ctypes.data for x in ids])
+    g, goff = _host_u8(genomes), _host_u64(genome_offsets)
+    G = len(goff) - 1
+    sp = IndexParams(k, w, canonical, 0)
+    p = classify_params(**params)
+    st = Stats()
+    if _is_torch(reads) and reads.is_cuda:
+        n_reads = offsets.numel() - 1
+        out = _part_outputs(reads.device, n_reads, p.top_n, G, want_locs)
+        rp, nb, op, dev = _ptr(reads), reads.numel(), _ptr(offsets), 1
+    else:
+        r, off = _host_u8(reads), _host_u64(offsets)
+        n_reads = len(off) - 1
+        out = _part_outputs(None, n_reads, p.top_n, G, want_locs)
+        rp, nb, op, dev = _ptr(r), len(r), _ptr(off), 0
+    _check(lib().mt_classify_partitioned(hv, iv, B, _ptr(g), _ptr(goff), G, ctypes.byref(sp), rp, nb, op, n_reads,
+                                         ctypes.byref(p), dev, _stream(stream), _ptr(out["taxon"]), _ptr(out["nloc"]),
+                                         _ptr(out["locs"]), _ptr(out["genome_hits"]), _ptr(out["abundance"]),
+                                         ctypes.byref(st)), "mt_classify_partitioned")
+    out["stats"] = st.as_dict()
+    return out
 
 
 class Plan:

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmt.so")
-SOURCES = ["index.cu", "index_io.cu", "eda.cu", "classify.cu", "server.cu", "profile.cu"]
+SOURCES = ["index.cu", "index_io.cu", "eda.cu", "classify.cu", "server.cu", "profile.cu", "partition.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

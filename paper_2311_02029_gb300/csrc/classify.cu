@@ -1635,6 +1635,14 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
     return status_of(h.err);
 }
 
+// The containment cutoff over given counts (used by the partitioned-database query).
+int mt::launch_mask(const uint64_t *hits, uint32_t G, uint32_t cont_num, uint32_t cont_den, uint8_t *keep,
+                    cudaStream_t s) {
+    k_mask<<<1, 1024, 0, s>>>((const unsigned long long *)hits, G, cont_num, cont_den, keep);
+    MT_CK(cudaGetLastError());
+    return MT_OK;
+}
+
 // ---- plans: preallocated workspace + captured CUDA graph ---------------------------------------------
 struct mt_plan {
     const mt_index *ix = nullptr;

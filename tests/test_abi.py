@@ -70,6 +70,46 @@ def test_status_strings_and_argument_checks_without_gpu(mtlib):
     assert L.mt_strerror(mtlib.MT_EXCHANGE) != L.mt_strerror(-99)
 
 
+def test_partitioned_query_argument_checks_without_gpu(mtlib):
+    L = mtlib.lib()
+    out = ctypes.c_void_p()
+    off = np.array([0, 4], np.uint64)
+    r = np.frombuffer(b"ACGT", np.uint8)
+    assert L.mt_part_create(0, ctypes.c_void_p(r.ctypes.data), 4, ctypes.c_void_p(off.ctypes.data), 1, 0, None,
+                            ctypes.byref(out)) == mtlib.MT_EINVAL          # no genomes
+    assert L.mt_part_create(3, None, 4, ctypes.c_void_p(off.ctypes.data), 1, 0, None,
+                            ctypes.byref(out)) == mtlib.MT_EINVAL          # no reads buffer
+    assert not out.value
+    assert L.mt_part_contain(None, None, None, 16) == mtlib.MT_EINVAL
+    assert L.mt_part_subset(None, 1, 10000, None, None, None, None) == mtlib.MT_EINVAL
+    cp = mtlib.classify_params()
+    assert L.mt_part_classify(None, None, None, 0, ctypes.byref(cp), None, None, None, None, None) == mtlib.MT_EINVAL
+    L.mt_part_destroy(None)
+    g = np.frombuffer(b"ACGT" * 10, np.uint8)
+    goff = np.array([0, 40], np.uint64)
+    sp = mtlib.IndexParams(15, 10, 1, mtlib.MT_INDEX_HPC)   # a subset index must support mapping
+    assert L.mt_classify_partitioned(None, None, 0, ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(goff.ctypes.data),
+                                     1, ctypes.byref(sp), ctypes.c_void_p(r.ctypes.data), 4,
+                                     ctypes.c_void_p(off.ctypes.data), 1, ctypes.byref(cp), 0, None, None, None,
+                                     None, None, None, None) == mtlib.MT_EINVAL
+
+
+@pytest.mark.parametrize("n_batches", [1, 2, 5, 25, 40])
+def test_split_batches(mtlib, n_batches):
+    """Consecutive ids, every genome once, no empty batch, about equal bases per batch."""
+    rng = np.random.default_rng(n_batches)
+    lens = rng.integers(1_000, 50_000, 40)
+    off = np.concatenate([[7], 7 + np.cumsum(lens)]).astype(np.uint64)
+    parts = mtlib.split_batches(off, n_batches)
+    assert len(parts) == n_batches and all(len(x) > 0 for x in parts)
+    assert np.array_equal(np.concatenate(parts), np.arange(40))
+    sizes = [int(lens[x].sum()) for x in parts]
+    if n_batches <= 5:   # each batch within one genome of its share
+        assert max(sizes) - min(sizes) <= 2 * int(lens.max())
+    with pytest.raises(ValueError):
+        mtlib.split_batches(off, 41)
+
+
 def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     import paper_2311_02029_gb300 as mt
     monkeypatch.setattr(mt, "_lib", None)
