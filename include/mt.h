@@ -233,7 +233,8 @@ int mt_classify_masked(const mt_index *ix, const uint8_t *reads, uint64_t n_base
  * one of its genomes changes, rebuilt without touching the others); a batch's genomes carry
  * global ids 0..n_genomes-1, and one genome may sit in several batches. One read batch is
  * classified against it in the paper's order:
- *  1. mt_part_contain, once per database batch: that batch's seed hits per genome over all the
+ *  1. mt_part_contain, once per database batch (or mt_part_contain_batches for several resident
+ *     batches at once): that batch's seed hits per genome over all the
  *     reads, with the batch's own repeat filter (max_occ counts occurrences in that batch); a
  *     genome keeps the highest count any batch gave it;
  *  2. mt_part_subset: the normalised cutoff over the whole database, keep[g] =
@@ -260,6 +261,13 @@ int mt_part_create(uint32_t n_genomes, const uint8_t *reads, uint64_t n_bases, c
  * Errors: MT_EINVAL (NULL arguments, an id out of range, max_occ above MT_MAX_OCC_LIMIT, bad
  * reads or offsets), MT_ENOMEM, MT_ECUDA. */
 int mt_part_contain(mt_part *q, const mt_index *batch, const uint32_t *genome_ids, uint32_t max_occ);
+/* Stage 1 for several resident database batches in one pass over the reads: each read's
+ * minimizers are found once and looked up in every batch's table. Same counts as one
+ * mt_part_contain per batch. genome_ids[b]: as in mt_part_contain for batches[b]. The batches
+ * must share k, w, canonical and MT_INDEX_HPC.
+ * Errors: those of mt_part_contain; MT_EINVAL for batches built with different seeds. */
+int mt_part_contain_batches(mt_part *q, const mt_index *const *batches, const uint32_t *const *genome_ids,
+                            uint32_t n_batches, uint32_t max_occ);
 /* The cutoff over the counts gathered so far. Outputs (each may be NULL): keep[n_genomes] (host),
  * genome_hits[n_genomes] (the highest counts; host or device like the reads), kept (host,
  * n_genomes entries of room: the kept global ids, increasing) and *n_kept.

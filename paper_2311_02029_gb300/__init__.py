@@ -85,7 +85,7 @@ EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", 
            "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_containment", "mt_classify_masked", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
-           "mt_server_cancel", "mt_server_destroy", "mt_part_create", "mt_part_contain", "mt_part_subset",
+           "mt_server_cancel", "mt_server_destroy", "mt_part_create", "mt_part_contain", "mt_part_contain_batches", "mt_part_subset",
            "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned"]
 
 
@@ -152,6 +152,8 @@ def lib():
         L.mt_part_create.argtypes = [u32, vp, u64, vp, u64, i32, vp, ctypes.POINTER(vp)]
         L.mt_part_contain.restype = i32
         L.mt_part_contain.argtypes = [vp, vp, vp, u32]
+        L.mt_part_contain_batches.restype = i32
+        L.mt_part_contain_batches.argtypes = [vp, vp, vp, u32, u32]
         L.mt_part_subset.restype = i32
         L.mt_part_subset.argtypes = [vp, u32, u32, vp, vp, vp, ctypes.POINTER(u32)]
         L.mt_part_classify.restype = i32
@@ -475,6 +477,19 @@ class PartitionedQuery:
         if len(ids) != batch.n_genomes:
             raise ValueError("one global id per genome of the batch")
         _check(lib().mt_part_contain(self._h, batch.handle, _ptr(ids), max_occ), "mt_part_contain")
+
+    def contain_batches(self, batches, genome_ids, max_occ: int = 1024):
+        """``mt_part_contain_batches``: several resident batches (same seeds) in one pass."""
+        if len(batches) != len(genome_ids):
+            raise ValueError("one id list per batch")
+        ids = [np.ascontiguousarray(x, dtype=np.uint32) for x in genome_ids]
+        for ix, x in zip(batches, ids):
+            if len(x) != ix.n_genomes:
+                raise ValueError("one global id per genome of each batch")
+        B = len(batches)
+        hv = (ctypes.c_void_p * max(B, 1))(*[ix.handle.value for ix in batches])
+        iv = (ctypes.c_void_p * max(B, 1))(*[x.ctypes.data for x in ids])
+        _check(lib().mt_part_contain_batches(self._h, hv, iv, B, max_occ), "mt_part_contain_batches")
 
     def subset(self, cont_num: int = 1, cont_den: int = 10000) -> dict:
         G = self.n_genomes

@@ -84,6 +84,15 @@ struct Counters {
     uint32_t pad2;
 };
 
+// one index among several counted in one pass
+struct BatchView {
+    const ulonglong2 *table;
+    uint64_t slot_mask;
+    const uint64_t *occ;
+    uint32_t slot_shift;
+    uint32_t base;          // first counter of the batch's genomes
+};
+
 struct SeedArgs {
     IndexView ix;
     const IoBlock *io;
@@ -95,6 +104,10 @@ struct SeedArgs {
     uint32_t *fb_list;
     Counters *ctr;
     uint64_t r_begin, r_end;   // the reads this launch takes: [r_begin, min(r_end, n_reads))
+    // counting over several indexes of one (k, w, canonical, compression) at once: every
+    // minimizer is looked up in each batch's table and counted at base + genome
+    const BatchView *bv = nullptr;
+    uint32_t n_bv = 0, n_hist = 0;
 };
 
 // ---- read packing (one warp) ------------------------------------------------------------
@@ -348,12 +361,13 @@ MT_DEV void sort_hits(T *h, uint32_t H) {
 // COUNT: containment only (every occurrence of every minimizer counted per genome, no
 // locations, no outputs per read); HPC: the reads' seeds are taken after homopolymer
 // compression (an index built with MT_INDEX_HPC).
-template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false>
+template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false>
 __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
+    static_assert(!MULTI || (COUNT && !HK32), "several indexes are only counted");
     using HitT = typename HitKey<HK32>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(smraw);
-    const uint32_t hist_n = SMEM_HIST ? A.ix.G : 0;
+    const uint32_t hist_n = SMEM_HIST ? (MULTI ? A.n_hist : A.ix.G) : 0;
     WarpSmem<HitT> *wsall = reinterpret_cast<WarpSmem<HitT> *>(smraw + ((hist_n * 8 + 15) & ~15u));
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     WarpSmem<HitT> &ws = wsall[warp];
@@ -488,6 +502,58 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             }
             __syncwarp();
             n_mins += nm;
+            if (MULTI) {
+                // (minimizer, batch) pairs spread over the lanes, each one lookup in that
+                // batch's table; matches counted straight into the batch's genome counters
+                const uint32_t B = A.n_bv, np = nm * B;
+                for (uint32_t p0 = 0; p0 < np; p0 += 32) {
+                    const uint32_t pq = p0 + lane;
+                    uint32_t cnt = 0, ni = 0, base = 0;
+                    uint64_t w1 = 0, w2 = 0, w3 = 0;
+                    const uint64_t *occ = nullptr;
+                    if (pq < np) {
+                        const uint32_t m = pq / B, b = pq - m * B;
+                        const BatchView bv = A.bv[b];
+                        const uint32_t xi = ws.u.t.mpos[m] - t0;
+                        const uint64_t want = (ws.u.t.code[xi] & CODE_MASK62) + 1;
+                        uint64_t s = slot_of(ws.u.t.key[xi], bv.slot_shift);
+                        for (uint64_t it = 0; it <= bv.slot_mask; it++) {
+                            const ulonglong2 a = __ldg(&bv.table[2 * s]);
+                            const ulonglong2 c2 = __ldg(&bv.table[2 * s + 1]);
+                            if (a.x == 0) break;
+                            if ((a.x & CODE_MASK62) == want) {
+                                ni = (uint32_t)(a.x >> 62);
+                                w1 = a.y; w2 = c2.x; w3 = c2.y;
+                                cnt = ni ? ni : (uint32_t)(a.y >> 40);
+                                break;
+                            }
+                            s = (s + 1) & bv.slot_mask;
+                        }
+                        if (cnt > A.max_occ) cnt = 0;
+                        if (!ni) n_ext += cnt;
+                        base = bv.base;
+                        occ = bv.occ;
+                    }
+                    H += __shfl_sync(FULL, warp_incl_scan(cnt), 31);
+                    if (ni && cnt) {
+#pragma unroll
+                        for (uint32_t t = 0; t < 3; t++)
+                            if (t < cnt) atomicAdd(&H_out[base + ((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33)], 1ull);
+                    }
+                    unsigned ext = __ballot_sync(FULL, ni == 0 && cnt != 0);
+                    while (ext) {
+                        const int src = __ffs(ext) - 1;
+                        ext &= ext - 1;
+                        const uint32_t c = __shfl_sync(FULL, cnt, src);
+                        const uint32_t bb = __shfl_sync(FULL, base, src);
+                        const uint64_t off = __shfl_sync(FULL, w1 & OFF_MASK40, src);
+                        const uint64_t *oc = (const uint64_t *)__shfl_sync(FULL, (unsigned long long)occ, src);
+                        for (uint32_t q = lane; q < c; q += 32) atomicAdd(&H_out[bb + (__ldg(&oc[off + q]) >> 33)], 1ull);
+                    }
+                }
+                __syncwarp();
+                continue;
+            }
             // Index lookups, one minimizer a lane, both halves of a slot loaded together; then
             // the round's matches are expanded across the warp.
             for (uint32_t m0 = 0; m0 < nm; m0 += 32) {
@@ -1186,14 +1252,15 @@ static int exchange(const EnqueueCtx &c, cudaStream_t s, void *dev, uint32_t G, 
     return MT_OK;
 }
 
-template <bool SH, bool HK32, bool COUNT = false, bool HPC = false>
+template <bool SH, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false>
 static int launch_seed(const SeedArgs &A, size_t smem, uint64_t need, cudaStream_t s) {
-    MT_CK(cudaFuncSetAttribute(k_seed<SH, HK32, COUNT, HPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = k_seed<SH, HK32, COUNT, HPC, MULTI>;
+    MT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed<SH, HK32, COUNT, HPC>, SEED_THREADS, smem));
+    MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SEED_THREADS, smem));
     per_sm = std::max(per_sm, 1);
     const unsigned grid = (unsigned)std::min<uint64_t>(need, (uint64_t)sm_count() * per_sm);
-    k_seed<SH, HK32, COUNT, HPC><<<grid, SEED_THREADS, smem, s>>>(A);
+    kern<<<grid, SEED_THREADS, smem, s>>>(A);
     MT_CK(cudaGetLastError());
     return MT_OK;
 }
@@ -1628,6 +1695,85 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
     const cudaMemcpyKind kind = host_io ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     if (cudaMemcpyAsync(genome_hits, ghits, G * 8ull, kind, s) != cudaSuccess) return fail(MT_ECUDA);
     if (keep && cudaMemcpyAsync(keep, dkeep, G, kind, s) != cudaSuccess) return fail(MT_ECUDA);
+    Counters h{};
+    if (cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MT_ECUDA);
+    dfree(ws, s);
+    MT_CK(cudaStreamSynchronize(s));
+    return status_of(h.err);
+}
+
+// Seed hits of several indexes built with one (k, w, canonical, compression) in one pass over
+// device-resident reads: each read's minimizers are found once and looked up in every
+// index's table; hits[base_b + g] counts genome g of index b, base_b = the number of genomes
+// of the indexes before b. Equal to one counting pass per index.
+int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const uint8_t *reads, uint64_t n_bases,
+                      const uint64_t *offsets, uint64_t n_reads, uint32_t max_occ, uint64_t *hits, cudaStream_t s) {
+    if (!n_batches) return MT_OK;
+    if (!batches || !batches[0] || !hits || !offsets || (!reads && n_bases) || max_occ > MT_MAX_OCC_LIMIT)
+        return MT_EINVAL;
+    const mt_index *b0 = batches[0];
+    std::vector<BatchView> hv(n_batches);
+    uint64_t T = 0;
+    for (uint32_t b = 0; b < n_batches; b++) {
+        const mt_index *ix = batches[b];
+        if (!ix || ix->k != b0->k || ix->w != b0->w || ix->canonical != b0->canonical || ix->hpc != b0->hpc)
+            return MT_EINVAL;
+        hv[b].table = ix->d_table;
+        hv[b].slot_mask = ix->slots - 1;
+        hv[b].occ = ix->d_occ;
+        hv[b].slot_shift = ix->slot_shift;
+        hv[b].base = (uint32_t)T;
+        T += ix->G;
+    }
+    if (T >= (1ull << 31)) return MT_EINVAL;
+    uint64_t off0 = 0;
+    if (n_reads) {
+        MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
+        MT_CK(cudaStreamSynchronize(s));
+    }
+    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_io = up(sizeof(Counters)), o_bv = o_io + up(sizeof(IoBlock));
+    const size_t total = o_bv + up(n_batches * sizeof(BatchView));
+    unsigned char *ws = nullptr;
+    int rc = dalloc((void **)&ws, total, s);
+    if (rc) return rc;
+    auto fail = [&](int code) { dfree(ws, s); cudaStreamSynchronize(s); return code; };
+    Counters *ctr = (Counters *)ws;
+    IoBlock hio{};
+    hio.reads = reads;
+    hio.roff = offsets;
+    hio.n_reads = n_reads;
+    hio.n_bases = n_bases;
+    hio.off0 = off0;
+    hio.max_len = MT_MAX_READ_LEN;
+    hio.vec_ok = ((uintptr_t)reads & 15u) == 0;
+    if (cudaMemsetAsync(ctr, 0, sizeof(Counters), s) != cudaSuccess ||
+        cudaMemsetAsync(hits, 0, T * 8, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + o_io, &hio, sizeof(hio), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + o_bv, hv.data(), n_batches * sizeof(BatchView), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail(MT_ECUDA);
+    if (n_reads) {
+        SeedArgs A{};
+        A.ix = b0->view();
+        A.io = (const IoBlock *)(ws + o_io);
+        A.min_seeds = 1;
+        A.max_occ = max_occ;
+        A.ghits = (unsigned long long *)hits;
+        A.ctr = ctr;
+        A.r_begin = 0;
+        A.r_end = ~0ull;
+        A.bv = (const BatchView *)(ws + o_bv);
+        A.n_bv = n_batches;
+        A.n_hist = (uint32_t)T;
+        const bool smem_hist = T <= SMEM_HIST_MAX;
+        const size_t smem = (smem_hist ? ((T * 8 + 15) & ~15ull) : 0) + SEED_WARPS * sizeof(WarpSmem<uint64_t>);
+        const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
+        if (b0->hpc) rc = smem_hist ? launch_seed<true, false, true, true, true>(A, smem, need, s)
+                                    : launch_seed<false, false, true, true, true>(A, smem, need, s);
+        else rc = smem_hist ? launch_seed<true, false, true, false, true>(A, smem, need, s)
+                            : launch_seed<false, false, true, false, true>(A, smem, need, s);
+        if (rc) return fail(rc);
+    }
     Counters h{};
     if (cudaMemcpyAsync(&h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess) return fail(MT_ECUDA);
     dfree(ws, s);

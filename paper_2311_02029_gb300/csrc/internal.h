@@ -75,6 +75,10 @@ uint64_t classify_ws_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_read
                            const mt_classify_params *p, uint32_t maxn, bool host_io);
 int launch_pack_seqs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint64_t *words,
                      uint64_t total_words, uint32_t *err, cudaStream_t s);
+// Seed hits of several indexes of one (k, w, canonical, compression) in one pass over device
+// reads; hits (device) gets the indexes' genome counters one after another.
+int contain_multi(const mt_index *const *batches, uint32_t n_batches, const uint8_t *reads, uint64_t n_bases,
+                  const uint64_t *offsets, uint64_t n_reads, uint32_t max_occ, uint64_t *hits, cudaStream_t s);
 // keep[g] = (hits[g] * cont_den > max(hits) * cont_num), on the device
 int launch_mask(const uint64_t *hits, uint32_t G, uint32_t cont_num, uint32_t cont_den, uint8_t *keep,
                 cudaStream_t s);

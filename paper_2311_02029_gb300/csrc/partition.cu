@@ -2,8 +2,9 @@
 // Organisation and Index Construction & Querying"; Evaluation Methodology).
 //
 // Stage 1 runs batch by batch with each batch's own index (the counting seeding kernel of
-// mt_containment); a genome keeps the highest count any batch gave it (one atomicMax per
-// genome slot). The normalised cutoff then runs over the whole database, and stages 2-3 run
+// mt_containment), or for all resident batches at once in one pass of that kernel that finds
+// each read's minimizers once and looks them up in every batch's table; a genome keeps the
+// highest count any batch gave it (one atomicMax per genome slot). The normalised cutoff then runs over the whole database, and stages 2-3 run
 // against the subset index of the kept genomes (mt_classify_masked, every subset genome
 // kept); the subset's genome ids are mapped back to global ids on the device. Between calls
 // the query holds only the reads and n_genomes-sized vectors, so database batches can pass
@@ -149,6 +150,40 @@ extern "C" int mt_part_contain(mt_part *q, const mt_index *batch, const uint32_t
     return done(cuda_ok(cudaStreamSynchronize(q->s), "part contain") ? MT_OK : MT_ECUDA);
 }
 
+extern "C" int mt_part_contain_batches(mt_part *q, const mt_index *const *batches, const uint32_t *const *genome_ids,
+                                       uint32_t n_batches, uint32_t max_occ) {
+    if (!q || (n_batches && (!batches || !genome_ids))) return MT_EINVAL;
+    if (!n_batches) return MT_OK;
+    uint64_t T = 0;
+    for (uint32_t b = 0; b < n_batches; b++) {
+        if (!batches[b] || !genome_ids[b]) return MT_EINVAL;
+        for (uint32_t l = 0; l < batches[b]->G; l++)
+            if (genome_ids[b][l] >= q->G) return MT_EINVAL;
+        T += batches[b]->G;
+    }
+    if (T >= (1ull << 31)) return MT_EINVAL;
+    // the batches' global ids one after another, like their counters
+    std::vector<uint32_t> ids;
+    ids.reserve(T);
+    for (uint32_t b = 0; b < n_batches; b++) ids.insert(ids.end(), genome_ids[b], genome_ids[b] + batches[b]->G);
+    Carver c;
+    const size_t o_hits = c.take<uint64_t>(T), o_ids = c.take<uint32_t>(T);
+    unsigned char *ws = nullptr;
+    int rc = dalloc((void **)&ws, c.off + 256, q->s);
+    if (rc) return rc;
+    uint64_t *hits = (uint64_t *)(ws + o_hits);
+    uint32_t *d_ids = (uint32_t *)(ws + o_ids);
+    auto done = [&](int code) { dfree(ws, q->s); cudaStreamSynchronize(q->s); return code; };
+    if (!cuda_ok(cudaMemcpyAsync(d_ids, ids.data(), T * 4, cudaMemcpyHostToDevice, q->s), "part ids"))
+        return done(MT_ECUDA);
+    rc = contain_multi(batches, n_batches, q->reads, q->n_bases, q->roff, q->n_reads, max_occ, hits, q->s);
+    if (rc) return done(rc);
+    k_part_max<<<grid_for(T), 256, 0, q->s>>>((const unsigned long long *)hits, d_ids, (uint32_t)T, q->H);
+    if (!cuda_ok(cudaGetLastError(), "k_part_max")) return done(MT_ECUDA);
+    q->have_subset = false;
+    return done(cuda_ok(cudaStreamSynchronize(q->s), "part contain") ? MT_OK : MT_ECUDA);
+}
+
 extern "C" int mt_part_subset(mt_part *q, uint32_t cont_num, uint32_t cont_den, uint8_t *keep, uint64_t *genome_hits,
                               uint32_t *kept, uint32_t *n_kept) {
     if (!q || cont_den == 0) return MT_EINVAL;
@@ -252,7 +287,14 @@ extern "C" int mt_classify_partitioned(const mt_index *const *batches, const uin
     mt_part *q = nullptr;
     int rc = mt_part_create(n_genomes, reads, n_bases, offsets, n_reads, device_ptrs, stream, &q);
     if (rc) return rc;
-    for (uint32_t b = 0; b < n_batches && !rc; b++) rc = mt_part_contain(q, batches[b], genome_ids[b], p->max_occ);
+    // one pass over the reads for all batches when they share their seeds' parameters
+    bool same = n_batches > 0;
+    for (uint32_t b = 0; b < n_batches && same; b++)
+        same = batches[b] && batches[b]->k == batches[0]->k && batches[b]->w == batches[0]->w &&
+               batches[b]->canonical == batches[0]->canonical && batches[b]->hpc == batches[0]->hpc;
+    if (same) rc = mt_part_contain_batches(q, batches, genome_ids, n_batches, p->max_occ);
+    else
+        for (uint32_t b = 0; b < n_batches && !rc; b++) rc = mt_part_contain(q, batches[b], genome_ids[b], p->max_occ);
     std::vector<uint32_t> kept(n_genomes);
     uint32_t nk = 0;
     if (!rc) rc = mt_part_subset(q, p->cont_num, p->cont_den, nullptr, genome_hits, kept.data(), &nk);

@@ -127,6 +127,47 @@ def test_mid_sized_database_in_25_batches(mt):
     compare_classify(got, ref)
 
 
+@pytest.mark.parametrize("hpc,many", [(False, False), (True, False), (False, True)])
+def test_one_pass_over_all_batches_equals_one_pass_each(mt, hpc, many):
+    """mt_part_contain_batches (each read's minimizers found once, looked up in every batch)
+    gives the counts of one mt_part_contain per batch, and the oracle's. ``many``: more genome
+    counters than fit in shared memory (4,200 small genomes)."""
+    import torch
+    if many:
+        c = gen.config(2, n_genomes=4200, genome_len=2_000, clade_size=10, n_reads=3_000, seed=61)
+    else:
+        c = gen.config(2, n_genomes=30, genome_len=40_000, clade_size=5, n_reads=6_000, seed=62)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    parts = _parts_with_copies(mt, g, 7)
+    k, w = (28, 18) if hpc else (c["k"], c["w"])
+    bs = [mt.Index(*oracle.gather_genomes(g.seq, g.offsets, ids), k, w, 1, hpc=hpc) for ids in parts]
+    dev = torch.device("cuda:0")
+    reads = torch.from_numpy(r.seq).to(dev)
+    offs = torch.from_numpy(r.offsets.astype(np.int64)).to(dev)
+    res = []
+    for fused in (True, False):
+        q = mt.PartitionedQuery(g.n, reads, offs)
+        if fused:
+            q.contain_batches(bs, parts, max_occ=3)
+        else:
+            for ix, ids in zip(bs, parts):
+                q.contain(ix, ids, max_occ=3)
+        res.append(as_np(q.subset(1, 10000)["genome_hits"]).astype(np.uint64))
+        q.close()
+    assert np.array_equal(res[0], res[1])
+    ora_b = [(oracle.Index(*oracle.gather_genomes(g.seq, g.offsets, ids), k, w, 1, compressed=hpc), ids)
+             for ids in parts]
+    ref = oracle.partitioned_hits(ora_b, g.n, r.seq, r.offsets, 3, threads=8)
+    assert np.array_equal(res[0], ref) and ref.sum() > 0
+    # batches whose seeds differ cannot share one pass
+    other = mt.Index(*oracle.gather_genomes(g.seq, g.offsets, parts[0]), k - 1, w, 1, hpc=hpc)
+    q = mt.PartitionedQuery(g.n, reads, offs)
+    with pytest.raises(mt.MtError):
+        q.contain_batches([bs[1], other], [parts[1], parts[0]])
+    q.close()
+
+
 def test_nothing_kept_and_empty_batch(mt):
     c, g, _ = _work(n_genomes=10, genome_len=20_000, clade=5, n_reads=10)
     parts = mt.split_batches(g.offsets, 3)
