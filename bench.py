@@ -449,7 +449,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and args.part_batches > 0:
         t0 = time.time()
         pids = mt.split_batches(g.offsets, args.part_batches)
-        pbs = [mt.Index(*mt.gather_genomes(g.seq, g.offsets, ids), 28, 18, 1, hpc=True) for ids in pids]
+        pbs = [mt.Index.subset(g.seq, g.offsets, ids, 28, 18, 1, hpc=True) for ids in pids]
         pbuild = time.time() - t0
         prm = params(c, mt.MT_EDA_BATCHED)
 
@@ -463,7 +463,7 @@ def run_ours(args):
                     q.contain(bix, ids, max_occ=prm["max_occ"])
             t.append(time.perf_counter())
             kept = q.subset(prm["cont_num"], prm["cont_den"])["kept"]
-            six = mt.Index(*mt.gather_genomes(g.seq, g.offsets, kept), c["k"], c["w"], c["canonical"])
+            six = mt.Index.subset(g.seq, g.offsets, kept, c["k"], c["w"], c["canonical"])
             t.append(time.perf_counter())
             o = q.classify(six, **prm)
             t.append(time.perf_counter())

@@ -160,6 +160,13 @@ int mt_version(void);
 int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
                    const mt_index_params *params, void *stream, mt_index **out);
 void mt_free_index(mt_index *ix);
+/* mt_build_index over the genomes ids[0..n_ids) of a set of n_set genomes (genomes / offsets as
+ * in mt_build_index, n_set + 1 offsets): genome i of the new index is genome ids[i] of the set.
+ * The chosen genomes' bytes go to the device directly, without a host-side copy of the subset
+ * (e.g. the subset database of a partitioned query). Errors: those of mt_build_index; MT_EINVAL
+ * for NULL ids or an id >= n_set. */
+int mt_build_index_subset(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_set, const uint32_t *ids,
+                          uint32_t n_ids, const mt_index_params *params, void *stream, mt_index **out);
 
 /* ---- index persistence (Methods, "Index Construction & Querying": the index is built once
  * and queried many times, so building stays off the query path) ---------------------------

@@ -80,7 +80,7 @@ class IndexInfo(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
-EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_free_index",
+EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", "mt_build_index_subset", "mt_free_index",
            "mt_save_index", "mt_load_index", "mt_profile_rollup",
            "mt_index_get_info", "mt_classify", "mt_classify_sharded", "mt_containment", "mt_classify_masked", "mt_classify_workspace_bytes", "mt_pack_seqs",
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
@@ -104,6 +104,8 @@ def lib():
         L.mt_version.restype = i32
         L.mt_build_index.restype = i32
         L.mt_build_index.argtypes = [vp, vp, u32, ctypes.POINTER(IndexParams), vp, ctypes.POINTER(vp)]
+        L.mt_build_index_subset.restype = i32
+        L.mt_build_index_subset.argtypes = [vp, vp, u32, vp, u32, ctypes.POINTER(IndexParams), vp, ctypes.POINTER(vp)]
         L.mt_free_index.argtypes = [vp]
         L.mt_profile_rollup.restype = i32
         L.mt_profile_rollup.argtypes = [vp, u32, vp, vp, u32, vp]
@@ -234,6 +236,22 @@ class Index:
         _check(lib().mt_build_index(_ptr(g), _ptr(off), self.n_genomes, ctypes.byref(p),
                                     _stream(stream), ctypes.byref(h)), "mt_build_index")
         self._h = h
+
+    @classmethod
+    def subset(cls, genomes, offsets, ids, k: int, w: int, canonical: int = 1, stream=None, hpc: bool = False):
+        """``mt_build_index_subset``: an index over the genomes ``ids`` of a host genome set, in
+        that order, without a host-side copy of them."""
+        g = _host_u8(genomes)
+        off = _host_u64(offsets)
+        sel = np.ascontiguousarray(ids, dtype=np.uint32)
+        p = IndexParams(k, w, canonical, MT_INDEX_HPC if hpc else 0)
+        h = ctypes.c_void_p()
+        _check(lib().mt_build_index_subset(_ptr(g), _ptr(off), len(off) - 1, _ptr(sel), len(sel), ctypes.byref(p),
+                                           _stream(stream), ctypes.byref(h)), "mt_build_index_subset")
+        ix = cls.__new__(cls)
+        ix._h = h
+        ix.n_genomes = len(sel)
+        return ix
 
     @property
     def handle(self):

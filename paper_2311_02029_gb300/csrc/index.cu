@@ -278,18 +278,21 @@ __global__ void __launch_bounds__(HPC_THREADS) k_hpc_write(const uint8_t *seq, c
 
 using namespace mt;
 
-static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t G,
+// ids: genome g of the index is genome ids[g] of the set (its bytes copied straight to the
+// device, run by run of consecutive ids), or genome g itself when ids is null.
+static int build_impl(const uint8_t *genomes, const uint64_t *offsets, const uint32_t *ids, uint32_t G,
                       const mt_index_params *p, cudaStream_t s, mt_index *ix) {
-    const uint64_t off0 = offsets[0];
-    uint64_t total = offsets[G] - off0;
+    auto src = [&](uint32_t g) { return ids ? ids[g] : g; };
     for (uint32_t g = 0; g < G; g++) {
-        if (offsets[g + 1] < offsets[g]) return MT_EINVAL;
-        if (offsets[g + 1] - offsets[g] >= (1ull << 32)) return MT_EINVAL;
+        const uint64_t a = offsets[src(g)], b = offsets[src(g) + 1];
+        if (b < a) return MT_EINVAL;
+        if (b - a >= (1ull << 32)) return MT_EINVAL;
     }
     ix->G = G; ix->k = p->k; ix->w = p->w; ix->canonical = p->canonical ? 1 : 0;
     ix->hpc = (p->flags & MT_INDEX_HPC) ? 1 : 0;
-    std::vector<uint64_t> hoff(G + 1), hgword(G);
-    for (uint32_t g = 0; g <= G; g++) hoff[g] = offsets[g] - off0;
+    std::vector<uint64_t> hoff(G + 1, 0), hgword(G);
+    for (uint32_t g = 0; g < G; g++) hoff[g + 1] = hoff[g] + (offsets[src(g) + 1] - offsets[src(g)]);
+    uint64_t total = hoff[G];
 
     int rc = MT_OK;
     uint8_t *d_seq = nullptr;
@@ -299,7 +302,13 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t 
     if ((rc = dalloc((void **)&d_seq, std::max<uint64_t>(total, 1), s))) return rc;
     if ((rc = dalloc((void **)&d_off, (G + 1) * 8, s))) return rc;
     if ((rc = dalloc((void **)&d_err, 4, s))) return rc;
-    if (total) MT_CK(cudaMemcpyAsync(d_seq, genomes + off0, total, cudaMemcpyHostToDevice, s));
+    for (uint32_t g = 0; g < G && total;) {
+        uint32_t e = g + 1;   // a run of genomes adjacent in the set
+        while (e < G && offsets[src(e)] == offsets[src(e - 1) + 1]) e++;
+        const uint64_t bytes = hoff[e] - hoff[g];
+        if (bytes) MT_CK(cudaMemcpyAsync(d_seq + hoff[g], genomes + offsets[src(g)], bytes, cudaMemcpyHostToDevice, s));
+        g = e;
+    }
     MT_CK(cudaMemcpyAsync(d_off, hoff.data(), (G + 1) * 8, cudaMemcpyHostToDevice, s));
     if (ix->hpc) {   // the genomes are indexed in homopolymer-compressed form
         uint64_t *d_cnt = nullptr, *d_off2 = nullptr;
@@ -493,8 +502,8 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, uint32_t 
     return MT_OK;
 }
 
-extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
-                              const mt_index_params *p, void *stream, mt_index **out) {
+static int build_checked(const uint8_t *genomes, const uint64_t *offsets, const uint32_t *ids, uint32_t n_genomes,
+                         const mt_index_params *p, void *stream, mt_index **out) {
     if (!out) return MT_EINVAL;
     *out = nullptr;
     if (!genomes || !offsets || !p || n_genomes == 0 || n_genomes > MT_MAX_GENOMES) return MT_EINVAL;
@@ -502,7 +511,7 @@ extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, u
     cudaStream_t s = (cudaStream_t)stream;
     mt_index *ix = new mt_index();
     cudaGetDevice(&ix->device);
-    int rc = build_impl(genomes, offsets, n_genomes, p, s, ix);
+    int rc = build_impl(genomes, offsets, ids, n_genomes, p, s, ix);
     if (rc != MT_OK) {
         cudaStreamSynchronize(s);
         mt_free_index(ix);
@@ -510,6 +519,21 @@ extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, u
     }
     *out = ix;
     return MT_OK;
+}
+
+extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
+                              const mt_index_params *p, void *stream, mt_index **out) {
+    return build_checked(genomes, offsets, nullptr, n_genomes, p, stream, out);
+}
+
+extern "C" int mt_build_index_subset(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_set,
+                                     const uint32_t *ids, uint32_t n_ids, const mt_index_params *p, void *stream,
+                                     mt_index **out) {
+    if (out) *out = nullptr;
+    if (!ids) return MT_EINVAL;
+    for (uint32_t i = 0; i < n_ids; i++)
+        if (ids[i] >= n_set) return MT_EINVAL;
+    return build_checked(genomes, offsets, ids, n_ids, p, stream, out);
 }
 
 extern "C" const char *mt_last_cuda_error(void) { return mt::last_cuda_error(); }

@@ -298,17 +298,8 @@ extern "C" int mt_classify_partitioned(const mt_index *const *batches, const uin
     std::vector<uint32_t> kept(n_genomes);
     uint32_t nk = 0;
     if (!rc) rc = mt_part_subset(q, p->cont_num, p->cont_den, nullptr, genome_hits, kept.data(), &nk);
-    mt_index *sub = nullptr;
-    if (!rc && nk) {
-        // the subset database: the kept genomes' bytes, in kept order
-        std::vector<uint64_t> off(nk + 1, 0);
-        for (uint32_t i = 0; i < nk; i++)
-            off[i + 1] = off[i] + (genome_offsets[kept[i] + 1] - genome_offsets[kept[i]]);
-        std::vector<uint8_t> seq(std::max<uint64_t>(off[nk], 1));
-        for (uint32_t i = 0; i < nk; i++)
-            memcpy(seq.data() + off[i], genomes + genome_offsets[kept[i]], off[i + 1] - off[i]);
-        rc = mt_build_index(seq.data(), off.data(), nk, subset_params, stream, &sub);
-    }
+    mt_index *sub = nullptr;   // the subset database: an index over the kept genomes, in kept order
+    if (!rc && nk) rc = mt_build_index_subset(genomes, genome_offsets, n_genomes, kept.data(), nk, subset_params, stream, &sub);
     if (!rc) rc = mt_part_classify(q, sub, kept.data(), nk, p, taxon, nloc, locs, abundance, stats);
     if (sub) mt_free_index(sub);
     mt_part_destroy(q);

@@ -87,6 +87,13 @@ def test_partitioned_query_argument_checks_without_gpu(mtlib):
     L.mt_part_destroy(None)
     g = np.frombuffer(b"ACGT" * 10, np.uint8)
     goff = np.array([0, 40], np.uint64)
+    ip = mtlib.IndexParams(15, 10, 1, 0)
+    bad = np.array([0, 1], np.uint32)                       # id 1 is not in a one-genome set
+    assert L.mt_build_index_subset(ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(goff.ctypes.data), 1,
+                                   ctypes.c_void_p(bad.ctypes.data), 2, ctypes.byref(ip), None,
+                                   ctypes.byref(out)) == mtlib.MT_EINVAL
+    assert L.mt_build_index_subset(ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(goff.ctypes.data), 1, None, 1,
+                                   ctypes.byref(ip), None, ctypes.byref(out)) == mtlib.MT_EINVAL
     sp = mtlib.IndexParams(15, 10, 1, mtlib.MT_INDEX_HPC)   # a subset index must support mapping
     assert L.mt_classify_partitioned(None, None, 0, ctypes.c_void_p(g.ctypes.data), ctypes.c_void_p(goff.ctypes.data),
                                      1, ctypes.byref(sp), ctypes.c_void_p(r.ctypes.data), 4,

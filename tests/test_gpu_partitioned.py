@@ -168,6 +168,22 @@ def test_one_pass_over_all_batches_equals_one_pass_each(mt, hpc, many):
     q.close()
 
 
+def test_subset_index_equals_index_over_gathered_genomes(mt):
+    """mt_build_index_subset (bytes copied run by run from the set) answers like an index built
+    from the gathered bytes: ids out of order, with gaps, a repeat and adjacent runs."""
+    c, g, r = _work(n_genomes=20, genome_len=30_000, clade=5, n_reads=3_000, seed=71)
+    ids = np.array([7, 8, 9, 2, 15, 3, 4, 19, 0, 9], np.uint32)
+    a = mt.Index.subset(g.seq, g.offsets, ids, c["k"], c["w"], c["canonical"])
+    b = mt.Index(*oracle.gather_genomes(g.seq, g.offsets, ids), c["k"], c["w"], c["canonical"])
+    assert a.info() == b.info()
+    prm = _prm(c)
+    x = mt.classify(a, r.seq, r.offsets, **prm)
+    y = mt.classify(b, r.seq, r.offsets, **prm)
+    for k in ("taxon", "nloc", "genome_hits"):
+        assert np.array_equal(x[k], y[k])
+    assert np.array_equal(x["locs"], y["locs"]) and np.array_equal(x["abundance"], y["abundance"])
+
+
 def test_nothing_kept_and_empty_batch(mt):
     c, g, _ = _work(n_genomes=10, genome_len=20_000, clade=5, n_reads=10)
     parts = mt.split_batches(g.offsets, 3)
