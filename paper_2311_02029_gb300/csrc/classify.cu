@@ -41,7 +41,9 @@ static constexpr uint32_t HCAP = 256;                     // seed matches held p
 static constexpr uint32_t RDW = MT_MAX_READ_LEN / 32 + 2;
 static constexpr uint32_t CSTORE = 8;                     // locations stored per read
 static constexpr uint32_t QOVF = 0xFFFFFFFFu;
-static constexpr uint32_t SMEM_HIST_MAX = 4096;           // genomes counted in shared memory
+static constexpr uint32_t SMEM_HIST_MAX = 4096;
+static constexpr uint32_t MULTI_UNROLL = 4;     // key-filter loads in flight per lane (several indexes)
+static constexpr uint32_t MULTI_MAX = 4096;     // indexes counted in one pass (exact pair / n_bv)           // genomes counted in shared memory
 static constexpr int FB_CTAS = 16;
 static constexpr int FB_THREADS = 256;
 
@@ -89,8 +91,11 @@ struct BatchView {
     const ulonglong2 *table;
     uint64_t slot_mask;
     const uint64_t *occ;
+    const uint64_t *filter;   // the index's key filter: a key it rejects is not in the table
     uint32_t slot_shift;
-    uint32_t base;          // first counter of the batch's genomes
+    uint32_t filter_shift;
+    uint32_t base;            // first counter of the batch's genomes
+    uint32_t pad;
 };
 
 struct SeedArgs {
@@ -108,6 +113,7 @@ struct SeedArgs {
     // minimizer is looked up in each batch's table and counted at base + genome
     const BatchView *bv = nullptr;
     uint32_t n_bv = 0, n_hist = 0;
+    uint32_t div_magic = 0;    // ceil(2^32 / n_bv): pair / n_bv = umulhi(pair, div_magic) (n_bv > 1)
 };
 
 // ---- read packing (one warp) ------------------------------------------------------------
@@ -503,55 +509,94 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             __syncwarp();
             n_mins += nm;
             if (MULTI) {
-                // (minimizer, batch) pairs spread over the lanes, each one lookup in that
-                // batch's table; matches counted straight into the batch's genome counters
+                // (minimizer, batch) pairs: the batches' key filters (small, in L2) are tested
+                // four pairs a lane at a time, so four loads are in flight; the pairs that pass
+                // (about one batch per minimizer) are queued in the idle match buffer and
+                // probed one a lane, matches counted into the batch's genome counters.
                 const uint32_t B = A.n_bv, np = nm * B;
-                for (uint32_t p0 = 0; p0 < np; p0 += 32) {
-                    const uint32_t pq = p0 + lane;
-                    uint32_t cnt = 0, ni = 0, base = 0;
-                    uint64_t w1 = 0, w2 = 0, w3 = 0;
-                    const uint64_t *occ = nullptr;
-                    if (pq < np) {
-                        const uint32_t m = pq / B, b = pq - m * B;
-                        const BatchView bv = A.bv[b];
-                        const uint32_t xi = ws.u.t.mpos[m] - t0;
-                        const uint64_t want = (ws.u.t.code[xi] & CODE_MASK62) + 1;
-                        uint64_t s = slot_of(ws.u.t.key[xi], bv.slot_shift);
-                        for (uint64_t it = 0; it <= bv.slot_mask; it++) {
-                            const ulonglong2 a = __ldg(&bv.table[2 * s]);
-                            const ulonglong2 c2 = __ldg(&bv.table[2 * s + 1]);
-                            if (a.x == 0) break;
-                            if ((a.x & CODE_MASK62) == want) {
-                                ni = (uint32_t)(a.x >> 62);
-                                w1 = a.y; w2 = c2.x; w3 = c2.y;
-                                cnt = ni ? ni : (uint32_t)(a.y >> 40);
-                                break;
-                            }
-                            s = (s + 1) & bv.slot_mask;
-                        }
-                        if (cnt > A.max_occ) cnt = 0;
-                        if (!ni) n_ext += cnt;
-                        base = bv.base;
-                        occ = bv.occ;
-                    }
-                    H += __shfl_sync(FULL, warp_incl_scan(cnt), 31);
-                    if (ni && cnt) {
-#pragma unroll
-                        for (uint32_t t = 0; t < 3; t++)
-                            if (t < cnt) atomicAdd(&H_out[base + ((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33)], 1ull);
-                    }
-                    unsigned ext = __ballot_sync(FULL, ni == 0 && cnt != 0);
-                    while (ext) {
-                        const int src = __ffs(ext) - 1;
-                        ext &= ext - 1;
-                        const uint32_t c = __shfl_sync(FULL, cnt, src);
-                        const uint32_t bb = __shfl_sync(FULL, base, src);
-                        const uint64_t off = __shfl_sync(FULL, w1 & OFF_MASK40, src);
-                        const uint64_t *oc = (const uint64_t *)__shfl_sync(FULL, (unsigned long long)occ, src);
-                        for (uint32_t q = lane; q < c; q += 32) atomicAdd(&H_out[bb + (__ldg(&oc[off + q]) >> 33)], 1ull);
-                    }
-                }
+                // the match buffer is idle when counting: the queue in its first 1 KB, the
+                // tile's minimizer keys in minimizer order in its second
+                uint32_t *queue = reinterpret_cast<uint32_t *>(ws.hits);
+                uint64_t *mkey = reinterpret_cast<uint64_t *>(ws.hits) + HCAP / 2;
+                static_assert(HCAP / 2 >= TILE && HCAP >= 32 * (MULTI_UNROLL + 1), "queue and keys fit");
+                for (uint32_t m = lane; m < nm; m += 32) mkey[m] = ws.u.t.key[ws.u.t.mpos[m] - t0];
                 __syncwarp();
+                uint32_t nq = 0;
+                for (uint32_t p0 = 0; p0 < np; p0 += 32 * MULTI_UNROLL) {
+                    uint32_t pass = 0;
+                    // branch-free, so the four filter loads can be in flight together
+#pragma unroll
+                    for (uint32_t u = 0; u < MULTI_UNROLL; u++) {
+                        const uint32_t pq = min(p0 + u * 32 + lane, np - 1);
+                        const uint32_t m = B == 1 ? pq : __umulhi(pq, A.div_magic), b = pq - m * B;
+                        const uint64_t key = mkey[m];
+                        const uint64_t fb = filter_bits(key);
+                        const uint64_t v = __ldg(&A.bv[b].filter[filter_block(key, A.bv[b].filter_shift)]);
+                        pass |= (uint32_t)((v & fb) == fb && p0 + u * 32 + lane < np) << u;
+                    }
+#pragma unroll
+                    for (uint32_t u = 0; u < MULTI_UNROLL; u++) {
+                        const unsigned bal = __ballot_sync(FULL, (pass >> u) & 1u);
+                        if ((pass >> u) & 1u) queue[nq + __popc(bal & ((1u << lane) - 1u))] = p0 + u * 32 + lane;
+                        nq += __popc(bal);
+                    }
+                    __syncwarp();
+                    const bool last = p0 + 32 * MULTI_UNROLL >= np;
+                    uint32_t done = 0;
+                    for (; done < nq && (last || nq - done >= 32); done += 32) {
+                        const uint32_t qi = done + lane;
+                        uint32_t cnt = 0, ni = 0, base = 0;
+                        uint64_t w1 = 0, w2 = 0, w3 = 0;
+                        const uint64_t *occ = nullptr;
+                        if (qi < nq) {
+                            const uint32_t pq = queue[qi];
+                            const uint32_t m = B == 1 ? pq : __umulhi(pq, A.div_magic), b = pq - m * B;
+                            const BatchView bv = A.bv[b];
+                            const uint32_t xi = ws.u.t.mpos[m] - t0;
+                            const uint64_t want = (ws.u.t.code[xi] & CODE_MASK62) + 1;
+                            uint64_t s = slot_of(ws.u.t.key[xi], bv.slot_shift);
+                            for (uint64_t it = 0; it <= bv.slot_mask; it++) {
+                                const ulonglong2 a = __ldg(&bv.table[2 * s]);
+                                const ulonglong2 c2 = __ldg(&bv.table[2 * s + 1]);
+                                if (a.x == 0) break;
+                                if ((a.x & CODE_MASK62) == want) {
+                                    ni = (uint32_t)(a.x >> 62);
+                                    w1 = a.y; w2 = c2.x; w3 = c2.y;
+                                    cnt = ni ? ni : (uint32_t)(a.y >> 40);
+                                    break;
+                                }
+                                s = (s + 1) & bv.slot_mask;
+                            }
+                            if (cnt > A.max_occ) cnt = 0;
+                            if (!ni) n_ext += cnt;
+                            base = bv.base;
+                            occ = bv.occ;
+                        }
+                        H += __shfl_sync(FULL, warp_incl_scan(cnt), 31);
+                        if (ni && cnt) {
+#pragma unroll
+                            for (uint32_t t = 0; t < 3; t++)
+                                if (t < cnt) atomicAdd(&H_out[base + ((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33)], 1ull);
+                        }
+                        unsigned ext = __ballot_sync(FULL, ni == 0 && cnt != 0);
+                        while (ext) {
+                            const int src = __ffs(ext) - 1;
+                            ext &= ext - 1;
+                            const uint32_t c = __shfl_sync(FULL, cnt, src);
+                            const uint32_t bb = __shfl_sync(FULL, base, src);
+                            const uint64_t off = __shfl_sync(FULL, w1 & OFF_MASK40, src);
+                            const uint64_t *oc = (const uint64_t *)__shfl_sync(FULL, (unsigned long long)occ, src);
+                            for (uint32_t q = lane; q < c; q += 32) atomicAdd(&H_out[bb + (__ldg(&oc[off + q]) >> 33)], 1ull);
+                        }
+                    }
+                    // keep the unprobed tail (fewer than 32) at the front of the queue
+                    const uint32_t left = nq > done ? nq - done : 0;
+                    const uint32_t keep_v = lane < left ? queue[done + lane] : 0u;
+                    __syncwarp();
+                    if (lane < left) queue[lane] = keep_v;
+                    nq = left;
+                    __syncwarp();
+                }
                 continue;
             }
             // Index lookups, one minimizer a lane, both halves of a slot loaded together; then
@@ -1709,7 +1754,8 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
 int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const uint8_t *reads, uint64_t n_bases,
                       const uint64_t *offsets, uint64_t n_reads, uint32_t max_occ, uint64_t *hits, cudaStream_t s) {
     if (!n_batches) return MT_OK;
-    if (!batches || !batches[0] || !hits || !offsets || (!reads && n_bases) || max_occ > MT_MAX_OCC_LIMIT)
+    if (!batches || !batches[0] || !hits || !offsets || (!reads && n_bases) || max_occ > MT_MAX_OCC_LIMIT ||
+        n_batches > MULTI_MAX)
         return MT_EINVAL;
     const mt_index *b0 = batches[0];
     std::vector<BatchView> hv(n_batches);
@@ -1722,7 +1768,10 @@ int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const 
         hv[b].slot_mask = ix->slots - 1;
         hv[b].occ = ix->d_occ;
         hv[b].slot_shift = ix->slot_shift;
+        hv[b].filter = ix->d_filter;
+        hv[b].filter_shift = ix->filter_shift;
         hv[b].base = (uint32_t)T;
+        hv[b].pad = 0;
         T += ix->G;
     }
     if (T >= (1ull << 31)) return MT_EINVAL;
@@ -1765,6 +1814,7 @@ int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const 
         A.bv = (const BatchView *)(ws + o_bv);
         A.n_bv = n_batches;
         A.n_hist = (uint32_t)T;
+        A.div_magic = n_batches > 1 ? (uint32_t)(((1ull << 32) + n_batches - 1) / n_batches) : 0u;
         const bool smem_hist = T <= SMEM_HIST_MAX;
         const size_t smem = (smem_hist ? ((T * 8 + 15) & ~15ull) : 0) + SEED_WARPS * sizeof(WarpSmem<uint64_t>);
         const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;

@@ -48,6 +48,17 @@ MT_DEV uint64_t slot_of(uint64_t key, uint32_t shift) {
     return (key * 0x9E3779B97F4A7C15ull) >> shift;
 }
 
+// Key filter of an index: one 64-bit block per key, picked by the top bits of another
+// multiplicative hash; three bits from the key's low 18 bits (minimizer keys are small, so
+// their low bits carry the entropy). A key in the index always passes; another passes with
+// the blocks' fill rate cubed.
+MT_DEV uint64_t filter_block(uint64_t key, uint32_t shift) {
+    return (key * 0xD6E8FEB86659FD93ull) >> shift;
+}
+MT_DEV uint64_t filter_bits(uint64_t key) {
+    return (1ull << (key & 63)) | (1ull << ((key >> 6) & 63)) | (1ull << ((key >> 12) & 63));
+}
+
 // ASCII -> 2-bit code (A0 C1 G2 T3); sets *bad for any other byte.
 MT_DEV uint32_t base_code(uint32_t b, bool &bad) {
     uint32_t c = (b >> 1) & 3u;      // A->0 C->1 G->3 T->2

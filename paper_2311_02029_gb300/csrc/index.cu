@@ -233,6 +233,36 @@ __global__ void k_insert(const uint64_t *ucode, const uint32_t *ucount, const ui
     }
 }
 
+// ---- key filter -------------------------------------------------------------------------------
+// One pass over the table: every stored key sets its three bits in its block. 8-16 bits a key
+// (a power of two of blocks), so the filters of a few dozen batch indexes stay in L2.
+__global__ void k_key_filter(const unsigned long long *table, uint64_t slots, uint64_t *filter, uint32_t shift) {
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long w0 = table[4 * s];
+        if (!w0) continue;
+        const uint64_t key = mix64((w0 & CODE_MASK62) - 1);
+        atomicOr(reinterpret_cast<unsigned long long *>(&filter[filter_block(key, shift)]),
+                 (unsigned long long)filter_bits(key));
+    }
+}
+
+int build_key_filter(mt_index *ix, cudaStream_t s) {
+    uint64_t blocks = 1024;
+    while (blocks * 8 < ix->n_keys) blocks <<= 1;
+    uint32_t lg = 0;
+    while ((1ull << lg) < blocks) lg++;
+    if (ix->d_filter) cudaFree(ix->d_filter);
+    ix->d_filter = nullptr;
+    MT_CK(cudaMalloc((void **)&ix->d_filter, blocks * 8));
+    ix->filter_blocks = blocks;
+    ix->filter_shift = 64 - lg;
+    MT_CK(cudaMemsetAsync(ix->d_filter, 0, blocks * 8, s));
+    const unsigned grid = (unsigned)std::min<uint64_t>((ix->slots + 255) / 256, (uint64_t)sm_count() * 8);
+    k_key_filter<<<grid, 256, 0, s>>>((const unsigned long long *)ix->d_table, ix->slots, ix->d_filter, ix->filter_shift);
+    MT_CK(cudaGetLastError());
+    return MT_OK;
+}
+
 // ---- homopolymer compression (the containment index's seeds, minimap2's -H) ------------------
 // Each run of one repeated byte in a sequence becomes one byte; runs never join across
 // sequences. One block per sequence: count, then write in tiles of 4 bytes a thread with a
@@ -496,9 +526,10 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, const uin
     (void)occ_spare;
     dfree(d_code[0], s); dfree(d_code[1], s);
     dfree(d_ucount, s); dfree(d_uoff, s); dfree(d_nruns, s); dfree(d_err, s);
+    if (!h_err && (rc = build_key_filter(ix, s))) return rc;
     MT_CK(cudaStreamSynchronize(s));
     if (h_err) return MT_ECUDA;
-    ix->device_bytes = ix->ref_words * 8 + G * 16 + slots * 32 + nb;
+    ix->device_bytes = ix->ref_words * 8 + G * 16 + slots * 32 + nb + ix->filter_blocks * 8;
     return MT_OK;
 }
 
@@ -545,6 +576,7 @@ extern "C" void mt_free_index(mt_index *ix) {
     cudaFree(ix->d_glen);
     cudaFree(ix->d_table);
     cudaFree(ix->d_occ);
+    cudaFree(ix->d_filter);
     delete ix;
 }
 

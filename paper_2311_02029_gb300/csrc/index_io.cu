@@ -167,8 +167,9 @@ extern "C" int mt_load_index(const char *path, void *stream, mt_index **out) {
     if ((rc = read_dev(file.f, ix->d_occ, h.occ_bytes, stage.p, s))) return rc;
     char tr[8];
     if (fread(tr, 1, 8, file.f) != 8 || memcmp(tr, TRAILER, 8) != 0) return MT_EIO;
+    if ((rc = build_key_filter(ix.get(), s))) return rc;   // derived data: rebuilt, not stored
     MT_CK(cudaStreamSynchronize(s));
-    ix->device_bytes = ix->ref_words * 8 + h.G * 16ull + h.slots * 32 + h.occ_bytes;
+    ix->device_bytes = ix->ref_words * 8 + h.G * 16ull + h.slots * 32 + h.occ_bytes + ix->filter_blocks * 8;
     *out = ix.release();
     return MT_OK;
 }

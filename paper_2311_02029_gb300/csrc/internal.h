@@ -50,6 +50,9 @@ struct mt_index {
     uint64_t ref_words = 0;
     uint64_t *d_ref = nullptr, *d_gword = nullptr, *d_glen = nullptr, *d_occ = nullptr;
     ulonglong2 *d_table = nullptr;
+    uint64_t *d_filter = nullptr;   // key filter, filter_blocks 64-bit blocks (derived from the table)
+    uint64_t filter_blocks = 0;
+    uint32_t filter_shift = 0;
     uint64_t device_bytes = 0;
     std::vector<uint64_t> h_glen;
 
@@ -75,6 +78,8 @@ uint64_t classify_ws_bytes(const mt_index *ix, uint64_t n_bases, uint64_t n_read
                            const mt_classify_params *p, uint32_t maxn, bool host_io);
 int launch_pack_seqs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint64_t *words,
                      uint64_t total_words, uint32_t *err, cudaStream_t s);
+// (Re)builds the index's key filter from its table (after a build or a load).
+int build_key_filter(mt_index *ix, cudaStream_t s);
 // Seed hits of several indexes of one (k, w, canonical, compression) in one pass over device
 // reads; hits (device) gets the indexes' genome counters one after another.
 int contain_multi(const mt_index *const *batches, uint32_t n_batches, const uint8_t *reads, uint64_t n_bases,
