@@ -13,7 +13,9 @@ upper bounds by per-diagonal Hamming distance and by banded edit distance (no fa
 reject), a lower bound by all-obstacle columns, planted-truth mapping of error-free reads,
 and hand-computed abundance splits; for a database cut into batches, reduction to the
 single-index pipeline when no key reaches the repeat filter, highest-not-summed counts of a
-genome held by several batches, and brute-force per-batch repeat filtering. Parity unpinned (defined readings with no external
+genome held by several batches, and brute-force per-batch repeat filtering; for genome
+shards on separate devices, reduction to the single-index pipeline and a hand-worked merge by
+rank with a unique read whose best locations share one genome. Parity unpinned (defined readings with no external
 check): the location clustering rule, rank tie-breaks, the max_occ repeat filter and the
 multi-read split -- the CUDA path must still agree with them bit-exactly.
 """
@@ -354,6 +356,79 @@ def classify_partitioned(batches, n_genomes: int, genomes_seq, genomes_off, read
     a[kept] = m["abundance"]
     return dict(taxon=taxon, locs=locs, nloc=m["nloc"], multi=multi, U=U, genome_hits=H, keep=keep,
                 abundance=a, kept=kept)
+
+
+def _rank_key(L):
+    """Rank of a location (Fig. 1, 2c; "Empirically Determined Parameters"): seeds descending,
+    then genome, strand and window start ascending (one E per read, so the window start orders
+    like the first diagonal)."""
+    return (-int(L["seeds"]), int(L["genome"]), int(L["strand"]), int(L["wstart"]))
+
+
+def merge_and_decide(loc_lists, reads_off, p: dict, n_genomes: int):
+    """Per read, the location lists of several genome shards (each the shard's top_n with
+    their distances, global genome ids) merged by the rank key and cut to top_n; then the
+    decision and profile of a single index (reading of Fig. 1, 3a-b): accepted = distance <= E;
+    taxon = genome of the first accepted location at the smallest distance; unique when one
+    genome holds that distance, else multi-mapped over those genomes."""
+    tn = p["top_n"]
+    off = np.asarray(reads_off, dtype=np.uint64)
+    n = len(off) - 1
+    taxon = np.full(n, -1, np.int32)
+    nloc = np.zeros(n, np.uint8)
+    locs = np.zeros((n, tn), LOC_DTYPE)
+    locs["genome"] = -1
+    multi = np.full((n, tn), -1, np.int32)
+    U = np.zeros(n_genomes, np.uint64)
+    for r in range(n):
+        ln = int(off[r + 1] - off[r])
+        E = (ln * p["e_permille"]) // 1000 if p["e_permille"] else p["e_abs"]
+        cand = [L for lst in loc_lists for L in lst[r] if L["genome"] >= 0]
+        cand.sort(key=_rank_key)
+        cand = cand[:tn]
+        nloc[r] = len(cand)
+        for t, L in enumerate(cand):
+            locs[r, t] = L
+        acc = [L for L in cand if int(L["dist"]) <= E]
+        if not acc:
+            continue
+        best = min(int(L["dist"]) for L in acc)
+        S = []
+        for L in cand:
+            if int(L["dist"]) == best and int(L["genome"]) not in S:
+                S.append(int(L["genome"]))
+        taxon[r] = S[0]
+        if len(S) == 1:
+            U[S[0]] += 1
+        else:
+            multi[r, :len(S)] = S
+    a = abundance(U, multi, tn, p["abund_cutoff"])
+    return dict(taxon=taxon, locs=locs, nloc=nloc, multi=multi, U=U, abundance=a)
+
+
+def classify_genome_sharded(shards, n_genomes: int, reads_seq, reads_off, p: dict, threads: int = 1):
+    """One read batch against a database whose genomes are split over several shards (one per
+    device; disjoint global ids), every shard seeing every read: stage 1 counts each shard's
+    genomes with its own index, the cutoff runs over all counts; each shard maps the reads
+    against its kept genomes (its own index, masked); the shards' per-read location lists are
+    merged by the rank key (``merge_and_decide``) and decided once. ``shards``: a list of
+    (Index, global ids of its genomes)."""
+    s = _u8(reads_seq)
+    off = np.ascontiguousarray(reads_off, dtype=np.uint64)
+    H = np.zeros(n_genomes, np.uint64)
+    for ix, ids in shards:
+        H[np.asarray(ids, dtype=np.int64)] += count_hits_sharded(ix, s, off, p["max_occ"], threads)
+    keep = keep_mask(H, p["cont_num"], p["cont_den"])
+    lists = []
+    for ix, ids in shards:
+        ids = np.asarray(ids, dtype=np.int64)
+        m = map_subset(ix, s, off, np.arange(len(off) - 1), p, keep[ids], threads)
+        g = m["locs"]["genome"]
+        m["locs"]["genome"] = np.where(g >= 0, ids[np.maximum(g, 0)], -1)
+        lists.append(m["locs"])
+    out = merge_and_decide(lists, off, p, n_genomes)
+    out.update(genome_hits=H, keep=keep)
+    return out
 
 
 def map_subset(ix: Index, reads_seq, reads_off, idx, p: dict, keep: np.ndarray, threads: int = 1):

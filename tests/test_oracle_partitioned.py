@@ -139,3 +139,48 @@ def test_gather_genomes_keeps_order(oracle_lib):
     off = np.array([0, 3, 5, 6, 10], np.uint64)
     s, o = oracle.gather_genomes(seq, off, [3, 0])
     assert bytes(s) == b"TTTTAAA" and o.tolist() == [0, 4, 7]
+
+
+# ---------------------------------------------------------------------------------------
+# genome shards on separate devices: per-shard mapping, lists merged by the rank key
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_shards,max_occ,cont_den", [(1, 3, 10000), (2, 2048, 10000), (3, 2048, 10),
+                                                       (4, 2048, 10000)])
+def test_genome_shards_equal_single_index(oracle_lib, n_shards, max_occ, cont_den):
+    """Disjoint genome shards, every shard seeing every read: when no key reaches the repeat
+    filter (or with one shard) per-genome counts and locations are those of one index over all
+    genomes, so the merged top_n and the decision must equal the single-index pipeline (whose
+    decision the C oracle takes; the merge and decision here are separately written)."""
+    c, g, r = _db()
+    p = oracle.params(max_occ=max_occ, e_abs=c["e_abs"], e_permille=0, min_seeds=c["min_seeds"], cont_den=cont_den)
+    full = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    ref = oracle.classify(full, r.seq, r.offsets, p)
+    parts = _split(g.n, n_shards, 13 + n_shards)
+    got = oracle.classify_genome_sharded(_batches(g, c, parts), g.n, r.seq, r.offsets, p)
+    _same(got, ref)
+    assert np.array_equal(got["multi"], ref["multi"])
+    if n_shards > 1:
+        assert (ref["taxon"] >= 0).mean() > 0.5
+
+
+def test_merge_rank_order_hand_case(oracle_lib):
+    """Two shards' lists of one read (E = 4): seeds first, then genome, strand, window start;
+    the merged first three decide the read (distances 5 > E, 2, 2: best 2 in genomes 3 then 1)."""
+    def L(g, seeds, strand, wstart, dist):
+        x = np.zeros((), oracle.LOC_DTYPE)
+        x["genome"], x["seeds"], x["strand"], x["wstart"], x["dist"] = g, seeds, strand, wstart, dist
+        return x
+    none = L(-1, 0, 0, 0, 0)
+    # read 1: both best locations lie in genome 2 (two strands): unique, not multi-mapped
+    a = np.array([[L(3, 9, 0, 100, 2), L(5, 4, 1, 7, 1), none],
+                  [L(2, 6, 0, 10, 1), L(2, 6, 1, 400, 1), none]], oracle.LOC_DTYPE)
+    b = np.array([[L(1, 9, 1, 50, 5), L(1, 4, 0, 900, 0), L(1, 4, 0, 800, 2)],
+                  [none, none, none]], oracle.LOC_DTYPE)
+    p = oracle.params(e_abs=4, e_permille=0, top_n=3)
+    out = oracle.merge_and_decide([a, b], np.array([0, 100, 200], np.uint64), p, 6)
+    assert out["locs"][0]["genome"].tolist() == [1, 3, 1]
+    assert out["locs"][0]["wstart"].tolist() == [50, 100, 800]
+    assert out["taxon"][0] == 3 and out["multi"][0].tolist() == [3, 1, -1]
+    assert out["nloc"].tolist() == [3, 2]
+    assert out["taxon"][1] == 2 and out["multi"][1].tolist() == [-1, -1, -1]
+    assert out["U"].tolist() == [0, 0, 1, 0, 0, 0]
