@@ -330,12 +330,46 @@ int mt_classify_partitioned(const mt_index *const *batches, const uint32_t *cons
 #define MT_XCHG_GENOME_HITS 0
 #define MT_XCHG_UNIQUE 1
 #define MT_XCHG_MULTI 2
+#define MT_XCHG_HOLDERS 3     /* (uint64, mt_classify_genome_sharded) ranks holding each genome */
+#define MT_XCHG_LOCATIONS 4   /* (bytes, all-gather, mt_classify_genome_sharded) per-read locations */
 typedef int (*mt_allreduce_fn)(void *ctx, int kind, void *buf, uint64_t count);
+/* recv (n_ranks * bytes) must receive every rank's send buffer (bytes each), in rank order. */
+typedef int (*mt_allgather_fn)(void *ctx, int kind, const void *send, uint64_t bytes, void *recv);
 int mt_classify_sharded(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
                         const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
                         int device_ptrs, void *stream, mt_allreduce_fn allreduce, void *ctx,
                         int32_t *taxon, uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits,
                         double *abundance, mt_stats *stats);
+
+/* ---- one read batch against genome shards held by several processes (ranks) ---------------
+ * A database too large for one device, split by genome: rank r holds an index over its own
+ * genomes (global ids genome_ids in index order, increasing, so that rank ties between genomes
+ * break alike in a shard and in the database; the ranks' sets must be disjoint) and every
+ * rank sees every read of the batch. The call, made by every rank with the same reads and
+ * params, runs:
+ *  1. allreduce(MT_XCHG_HOLDERS, n_genomes uint64: 1 for each genome this rank holds): a
+ *     genome held twice makes every rank return MT_EINVAL;
+ *  2. stage 1 over this rank's genomes; allreduce(MT_XCHG_GENOME_HITS) sums the hits (each
+ *     genome counted by its one rank); the cutoff over the whole database;
+ *  3. stage 2 (mt_classify_masked) against this rank's kept genomes: each read's top_n
+ *     locations with their distances, in global ids;
+ *  4. allgather(MT_XCHG_LOCATIONS, n_reads * top_n locations a rank) and, on every rank, each
+ *     read's lists merged in rank order (seeds descending, then genome, strand, window start),
+ *     the first top_n decided and profiled as by a single index.
+ * With no key reaching the repeat filter (each rank filters by its own index) the outputs
+ * equal mt_classify over one index of all genomes. Outputs (every rank, whole batch, global
+ * genome ids) and reads / offsets / device_ptrs / stream as in mt_classify. The exchange
+ * buffers are host memory; the calls block the calling host thread only.
+ * Errors: those of mt_classify; MT_EINVAL (NULL allreduce / allgather, n_ranks 0, an id >=
+ * n_genomes or ids not increasing, an MT_INDEX_HPC shard, overlapping shards); a call that
+ * fails its argument checks
+ * returns before its first exchange; MT_EXCHANGE when an exchange function returns non-zero. */
+int mt_classify_genome_sharded(const mt_index *shard, const uint32_t *genome_ids, uint32_t n_genomes,
+                               uint32_t n_ranks, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
+                               uint64_t n_reads, const mt_classify_params *params, int device_ptrs, void *stream,
+                               mt_allreduce_fn allreduce, mt_allgather_fn allgather, void *ctx, int32_t *taxon,
+                               uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
+                               mt_stats *stats);
 
 /* ---- taxonomic roll-up of a profile (Fig. 1, 3b; "Taxonomic Profile Generation") -----------
  * A taxonomy is a forest over n_nodes taxa given by parent[] (-1 for a root); genome g sits at

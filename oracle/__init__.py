@@ -412,7 +412,11 @@ def classify_genome_sharded(shards, n_genomes: int, reads_seq, reads_off, p: dic
     genomes with its own index, the cutoff runs over all counts; each shard maps the reads
     against its kept genomes (its own index, masked); the shards' per-read location lists are
     merged by the rank key (``merge_and_decide``) and decided once. ``shards``: a list of
-    (Index, global ids of its genomes)."""
+    (Index, global ids of its genomes), the ids increasing within a shard (a shard ranks ties
+    between genomes by its own genome order, which then is the global one)."""
+    for _, ids in shards:
+        if np.any(np.diff(np.asarray(ids, dtype=np.int64)) <= 0):
+            raise OracleError("genome ids of a shard must increase")
     s = _u8(reads_seq)
     off = np.ascontiguousarray(reads_off, dtype=np.uint64)
     H = np.zeros(n_genomes, np.uint64)

@@ -23,9 +23,12 @@ MT_OK, MT_EINVAL, MT_ENOMEM, MT_ETIMEDOUT, MT_ECUDA, MT_ECANCELED, MT_EBUSY = 0,
 MT_EXCHANGE = -7
 MT_EIO = -8
 MT_INDEX_HPC = 1
-MT_XCHG_GENOME_HITS, MT_XCHG_UNIQUE, MT_XCHG_MULTI = 0, 1, 2
+MT_XCHG_GENOME_HITS, MT_XCHG_UNIQUE, MT_XCHG_MULTI, MT_XCHG_HOLDERS, MT_XCHG_LOCATIONS = 0, 1, 2, 3, 4
 # mt_allreduce_fn: int (*)(void *ctx, int kind, void *buf, uint64_t count)
 AllreduceFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64)
+# mt_allgather_fn: int (*)(void *ctx, int kind, const void *send, uint64_t bytes, void *recv)
+AllgatherFn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64,
+                               ctypes.c_void_p)
 MT_EDA_BATCHED, MT_EDA_PLAIN = 0, 1
 # approximations, OR-ed into eda_mode / mode with a form
 MT_EDA_SNAKE, MT_EDA_HAMMING, MT_EDA_BASE_COUNTING, MT_EDA_QGRAM, MT_EDA_SHD = 0x00, 0x10, 0x20, 0x30, 0x40
@@ -86,7 +89,7 @@ EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", 
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
            "mt_server_cancel", "mt_server_destroy", "mt_part_create", "mt_part_contain", "mt_part_contain_batches", "mt_part_subset",
-           "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned"]
+           "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned", "mt_classify_genome_sharded"]
 
 
 def lib():
@@ -162,6 +165,10 @@ def lib():
         L.mt_part_classify.argtypes = [vp, vp, vp, u32, ctypes.POINTER(ClassifyParams), vp, vp, vp, vp,
                                        ctypes.POINTER(Stats)]
         L.mt_part_destroy.argtypes = [vp]
+        L.mt_classify_genome_sharded.restype = i32
+        L.mt_classify_genome_sharded.argtypes = [vp, vp, u32, u32, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams),
+                                                 i32, vp, AllreduceFn, AllgatherFn, vp, vp, vp, vp, vp, vp,
+                                                 ctypes.POINTER(Stats)]
         L.mt_classify_partitioned.restype = i32
         L.mt_classify_partitioned.argtypes = [vp, vp, u32, vp, vp, u32, ctypes.POINTER(IndexParams), vp, u64, vp,
                                               u64, ctypes.POINTER(ClassifyParams), i32, vp, vp, vp, vp, vp, vp,
@@ -406,6 +413,70 @@ def dist_allreduce(group=None):
         res = t.cpu().numpy()
         arr[...] = res.view(arr.dtype) if arr.dtype == np.uint64 else res
     return fn
+
+
+def allgather_callback(fn, n_ranks: int) -> AllgatherFn:
+    """Wraps ``fn(kind, send, recv)`` as an ``mt_allgather_fn``: send is a uint8 numpy view of
+    this rank's buffer, recv one of n_ranks times its size that fn must fill with every rank's
+    buffer in rank order. An exception in fn is reported as a failed exchange."""
+    def tramp(ctx, kind, send, nbytes, recv):
+        try:
+            nb = int(nbytes)
+            snd = np.ctypeslib.as_array((ctypes.c_uint8 * max(nb, 1)).from_address(send))[:nb]
+            rcv = np.ctypeslib.as_array((ctypes.c_uint8 * max(nb * n_ranks, 1)).from_address(recv))[:nb * n_ranks]
+            fn(int(kind), snd, rcv)
+            return 0
+        except Exception:
+            return 1
+    return AllgatherFn(tramp)
+
+
+def dist_allgather(group=None):
+    """An exchange function for ``allgather_callback`` over a torch.distributed process group
+    (gloo: host tensors; nccl: the current CUDA device)."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(kind, send, recv):
+        t = torch.from_numpy(send.copy())
+        if dist.get_backend(group) == "nccl":
+            t = t.cuda()
+        parts = [torch.empty_like(t) for _ in range(dist.get_world_size(group))]
+        dist.all_gather(parts, t, group=group)
+        if len(send):
+            recv[...] = torch.cat([x.cpu() for x in parts]).numpy()
+    return fn
+
+
+def classify_genome_sharded(shard: Index, genome_ids, n_genomes: int, n_ranks: int, reads, offsets, allreduce,
+                            allgather, *, stream=None, want_locs=True, **params) -> dict:
+    """``mt_classify_genome_sharded``: this rank's genome shard (global ids ``genome_ids``) against
+    the whole read batch; ``allreduce(kind, buf)`` sums a vector over the ranks in place (see
+    ``dist_allreduce``), ``allgather(kind, send, recv)`` gathers byte buffers (see
+    ``dist_allgather``). Every rank gets the whole batch's outputs in global genome ids."""
+    ids = np.ascontiguousarray(genome_ids, dtype=np.uint32)
+    if len(ids) != shard.n_genomes:
+        raise ValueError("one global id per genome of the shard")
+    p = classify_params(**params)
+    st = Stats()
+    ar = allreduce_callback(allreduce)
+    ag = allgather_callback(allgather, n_ranks)
+    G = int(n_genomes)
+    if _is_torch(reads) and reads.is_cuda:
+        n_reads = offsets.numel() - 1
+        out = _part_outputs(reads.device, n_reads, p.top_n, G, want_locs)
+        rp, nb, op, dev = _ptr(reads), reads.numel(), _ptr(offsets), 1
+    else:
+        r, off = _host_u8(reads), _host_u64(offsets)
+        n_reads = len(off) - 1
+        out = _part_outputs(None, n_reads, p.top_n, G, want_locs)
+        rp, nb, op, dev = _ptr(r), len(r), _ptr(off), 0
+    _check(lib().mt_classify_genome_sharded(shard.handle, _ptr(ids), G, n_ranks, rp, nb, op, n_reads, ctypes.byref(p),
+                                            dev, _stream(stream), ar, ag, None, _ptr(out["taxon"]),
+                                            _ptr(out["nloc"]), _ptr(out["locs"]), _ptr(out["genome_hits"]),
+                                            _ptr(out["abundance"]), ctypes.byref(st)), "mt_classify_genome_sharded")
+    out["stats"] = st.as_dict()
+    return out
 
 
 def classify_sharded(ix: Index, reads, offsets, allreduce, *, stream=None, want_locs=True, out=None,

@@ -1123,6 +1123,127 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
     }
 }
 
+// ---- location lists of several genome shards: merged by rank, then decided --------------------
+struct MergeArgs {
+    const mt_loc *lists;      // list q of read r: lists[(q * n_reads + r) * top_n ...], rank order, genome -1 ends it
+    const uint64_t *roff;
+    uint64_t n_reads;
+    uint32_t R, top_n, e_abs, e_permille, G, hist;
+    int32_t *taxon;
+    uint8_t *nloc;
+    mt_loc *locs;
+    unsigned long long *U;
+    int32_t *multi_set;
+    uint32_t *multi_list;
+    Counters *ctr;
+};
+
+// rank order of locations: seeds descending, then genome, strand, window start ascending
+MT_DEV bool loc_before(const mt_loc &a, const mt_loc &b) {
+    if (a.seeds != b.seeds) return a.seeds > b.seeds;
+    if (a.genome != b.genome) return a.genome < b.genome;
+    if (a.strand != b.strand) return a.strand < b.strand;
+    return a.wstart < b.wstart;
+}
+
+// Thread per read: the t-th merged location is the first in rank order after the (t-1)-th
+// among every shard's list (the shards' genomes are disjoint, so no two locations tie); the
+// first top_n are decided like a single index's (k_decide).
+__global__ void __launch_bounds__(256) k_merge_decide(MergeArgs A) {
+    extern __shared__ unsigned long long s_mU[];
+    const uint32_t hist_n = A.hist ? A.G : 0;
+    for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x) s_mU[g] = 0;
+    __syncthreads();
+    unsigned long long *U = A.hist ? s_mU : A.U;
+    const uint32_t lane = threadIdx.x & 31u, tn = A.top_n;
+    for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < A.n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = r0 + threadIdx.x;
+        int32_t uniq = -1;
+        bool is_multi = false;
+        if (r < A.n_reads) {
+            const uint32_t E = edit_threshold((uint32_t)(A.roff[r + 1] - A.roff[r]), A.e_abs, A.e_permille);
+            uint32_t d[MT_MAX_TOPN];
+            int32_t gg[MT_MAX_TOPN];
+            uint32_t nl = 0;
+            mt_loc prev;
+            memset(&prev, 0, sizeof(prev));
+            for (uint32_t t = 0; t < tn; t++) {
+                bool found = false;
+                mt_loc best;
+                memset(&best, 0, sizeof(best));
+                for (uint32_t q = 0; q < A.R; q++) {
+                    const mt_loc *L = A.lists + (q * A.n_reads + r) * tn;
+                    for (uint32_t u = 0; u < tn; u++) {
+                        const mt_loc c = L[u];
+                        if (c.genome < 0) break;
+                        if (t > 0 && !loc_before(prev, c)) continue;
+                        if (!found || loc_before(c, best)) { best = c; found = true; }
+                    }
+                }
+                if (!found) break;
+                A.locs[r * tn + t] = best;
+                prev = best;
+                nl++;
+            }
+#pragma unroll
+            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+                d[t] = 0xFFu; gg[t] = -1;
+                if (t < nl) { d[t] = A.locs[r * tn + t].dist; gg[t] = A.locs[r * tn + t].genome; }
+            }
+            for (uint32_t t = nl; t < tn; t++) {
+                mt_loc L;
+                memset(&L, 0, sizeof(L));
+                L.genome = -1;
+                A.locs[r * tn + t] = L;
+            }
+            uint32_t best_d = E + 1;
+#pragma unroll
+            for (uint32_t t = 0; t < MT_MAX_TOPN; t++)
+                if (t < nl && d[t] <= E && d[t] < best_d) best_d = d[t];
+            int32_t tax = -1;
+            int32_t S[MT_MAX_TOPN];
+            uint32_t ns = 0;
+#pragma unroll
+            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+                S[t] = -1;
+                if (t < nl && best_d <= E && d[t] == best_d) {
+                    if (tax < 0) tax = gg[t];
+                    bool seen = false;
+#pragma unroll
+                    for (uint32_t q = 0; q < t; q++) seen |= (S[q] == gg[t]);
+                    if (!seen) { S[t] = gg[t]; ns++; }
+                }
+            }
+            A.taxon[r] = tax;
+            A.nloc[r] = (uint8_t)nl;
+            if (ns == 1) uniq = tax;
+            if (ns >= 2) {
+                is_multi = true;
+                uint32_t o = 0;
+#pragma unroll
+                for (uint32_t t = 0; t < MT_MAX_TOPN; t++)
+                    if (S[t] >= 0) { A.multi_set[r * tn + o] = S[t]; o++; }
+                for (uint32_t t = o; t < tn; t++) A.multi_set[r * tn + t] = -1;
+            }
+        }
+        const unsigned act = __ballot_sync(FULL, uniq >= 0);
+        if (uniq >= 0) {
+            const unsigned peers = __match_any_sync(act, uniq);
+            if (lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&U[uniq], (unsigned long long)__popc(peers));
+        }
+        const unsigned mb = __ballot_sync(FULL, is_multi);
+        unsigned long long base = 0;
+        if (lane == 0 && mb) base = atomicAdd(reinterpret_cast<unsigned long long *>(&A.ctr->multi_count), (unsigned long long)__popc(mb));
+        base = __shfl_sync(FULL, base, 0);
+        if (is_multi) A.multi_list[base + __popc(mb & ((1u << lane) - 1u))] = (uint32_t)r;
+    }
+    if (A.hist) {
+        __syncthreads();
+        for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x)
+            if (s_mU[g]) atomicAdd(&A.U[g], s_mU[g]);
+    }
+}
+
 // multi-mapped reads: split by the genomes' unique counts (equally when they have none)
 __global__ void k_multi(const uint32_t *multi_list, const Counters *ctr, const int32_t *multi_set, uint32_t top_n,
                         const unsigned long long *U, double *M) {
@@ -1830,6 +1951,48 @@ int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const 
     MT_CK(cudaStreamSynchronize(s));
     return status_of(h.err);
 }
+
+// Several genome shards' per-read location lists (device) merged by rank and decided: per-read
+// outputs and the abundance profile (device pointers), as a single index's stage 3.
+int mt::merge_decide(const mt_loc *lists, uint32_t R, const uint64_t *roff, uint64_t n_reads, uint32_t G,
+                     const mt_classify_params *p, int32_t *taxon, uint8_t *nloc, mt_loc *locs, double *abundance,
+                     cudaStream_t s) {
+    const uint32_t tn = p->top_n;
+    Carver c;
+    const size_t o_ctr = c.take<Counters>(1), o_U = c.take<uint64_t>(G), o_M = c.take<double>(G);
+    const size_t o_set = c.take<int32_t>(std::max<uint64_t>(n_reads * tn, 1));
+    const size_t o_list = c.take<uint32_t>(std::max<uint64_t>(n_reads, 1));
+    unsigned char *ws = nullptr;
+    int rc = dalloc((void **)&ws, c.off + 256, s);
+    if (rc) return rc;
+    auto done = [&](int code) { dfree(ws, s); cudaStreamSynchronize(s); return code; };
+    Counters *ctr = (Counters *)(ws + o_ctr);
+    unsigned long long *U = (unsigned long long *)(ws + o_U);
+    double *M = (double *)(ws + o_M);
+    if (cudaMemsetAsync(ws, 0, o_set, s) != cudaSuccess) return done(MT_ECUDA);
+    if (n_reads) {
+        MergeArgs A;
+        A.lists = lists; A.roff = roff; A.n_reads = n_reads;
+        A.R = R; A.top_n = tn; A.e_abs = p->e_abs; A.e_permille = p->e_permille; A.G = G;
+        A.hist = G <= SMEM_HIST_MAX;
+        A.taxon = taxon; A.nloc = nloc; A.locs = locs; A.U = U;
+        A.multi_set = (int32_t *)(ws + o_set); A.multi_list = (uint32_t *)(ws + o_list); A.ctr = ctr;
+        const size_t smem = A.hist ? G * 8ull : 0;
+        if (smem > 48 * 1024 && !cuda_ok(cudaFuncSetAttribute(k_merge_decide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                             (int)smem), "k_merge_decide smem"))
+            return done(MT_ECUDA);
+        const unsigned grid = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 8);
+        k_merge_decide<<<grid, 256, smem, s>>>(A);
+        if (!cuda_ok(cudaGetLastError(), "k_merge_decide")) return done(MT_ECUDA);
+        k_multi<<<(unsigned)sm_count() * 4, 256, 0, s>>>(A.multi_list, ctr, A.multi_set, tn, U, M);
+        if (!cuda_ok(cudaGetLastError(), "k_multi")) return done(MT_ECUDA);
+    }
+    k_abund<<<1, 1024, 0, s>>>(G, U, M, p->abund_cutoff, abundance);
+    if (!cuda_ok(cudaGetLastError(), "k_abund")) return done(MT_ECUDA);
+    return done(cuda_ok(cudaStreamSynchronize(s), "merge decide") ? MT_OK : MT_ECUDA);
+}
+
+int mt::check_classify_params(const mt_classify_params *p) { return check_params(p); }
 
 // The containment cutoff over given counts (used by the partitioned-database query).
 int mt::launch_mask(const uint64_t *hits, uint32_t G, uint32_t cont_num, uint32_t cont_den, uint8_t *keep,

@@ -84,6 +84,13 @@ int build_key_filter(mt_index *ix, cudaStream_t s);
 // reads; hits (device) gets the indexes' genome counters one after another.
 int contain_multi(const mt_index *const *batches, uint32_t n_batches, const uint8_t *reads, uint64_t n_bases,
                   const uint64_t *offsets, uint64_t n_reads, uint32_t max_occ, uint64_t *hits, cudaStream_t s);
+// Per-read location lists of R genome shards (device, rank order) merged by rank and decided:
+// taxon / nloc / locs (device, n_reads entries) and abundance (device, G).
+int merge_decide(const mt_loc *lists, uint32_t R, const uint64_t *roff, uint64_t n_reads, uint32_t G,
+                 const mt_classify_params *p, int32_t *taxon, uint8_t *nloc, mt_loc *locs, double *abundance,
+                 cudaStream_t s);
+// The argument checks of mt_classify's parameters (MT_OK or MT_EINVAL).
+int check_classify_params(const mt_classify_params *p);
 // keep[g] = (hits[g] * cont_den > max(hits) * cont_num), on the device
 int launch_mask(const uint64_t *hits, uint32_t G, uint32_t cont_num, uint32_t cont_den, uint8_t *keep,
                 cudaStream_t s);

@@ -27,7 +27,7 @@ __global__ void k_part_max(const unsigned long long *hits, const uint32_t *ids, 
 __global__ void k_part_ids(uint64_t n_reads, uint32_t top_n, const uint32_t *ids, int32_t *taxon, mt_loc *locs) {
     const uint64_t n = n_reads * top_n;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (i < n_reads) {
+        if (taxon && i < n_reads) {
             const int32_t t = taxon[i];
             if (t >= 0) taxon[i] = (int32_t)ids[t];
         }
@@ -304,4 +304,100 @@ extern "C" int mt_classify_partitioned(const mt_index *const *batches, const uin
     if (sub) mt_free_index(sub);
     mt_part_destroy(q);
     return rc;
+}
+
+// ---- genome shards on separate devices (one process each) ---------------------------------------
+// Every rank holds an index over its own genomes and sees every read. Exchanges, through the
+// caller's functions: which genomes each rank holds (a sum, to refuse shards that overlap),
+// the genome hits (a sum: each genome is counted by its one rank), and every rank's per-read
+// top_n locations (an all-gather), which each rank merges by rank and decides.
+extern "C" int mt_classify_genome_sharded(const mt_index *shard, const uint32_t *genome_ids, uint32_t n_genomes,
+                                          uint32_t n_ranks, const uint8_t *reads, uint64_t n_bases,
+                                          const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *p,
+                                          int device_ptrs, void *stream, mt_allreduce_fn allreduce,
+                                          mt_allgather_fn allgather, void *ctx, int32_t *taxon, uint8_t *nloc,
+                                          mt_loc *locs, uint64_t *genome_hits, double *abundance, mt_stats *stats) {
+    // every check that can fail on one rank alone comes before the first exchange
+    if (!shard || !genome_ids || !allreduce || !allgather || !offsets || n_genomes == 0 || n_ranks == 0 ||
+        (!taxon && n_reads) || (!reads && n_bases))
+        return MT_EINVAL;
+    if (shard->hpc || check_classify_params(p)) return MT_EINVAL;
+    if (n_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
+    // increasing ids: the shard's own rank order (ties by genome) is then the global one
+    for (uint32_t l = 0; l < shard->G; l++)
+        if (genome_ids[l] >= n_genomes || (l && genome_ids[l] <= genome_ids[l - 1])) return MT_EINVAL;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t G = n_genomes, Gs = shard->G, tn = p->top_n;
+    const uint64_t n = n_reads, per_rank = n * tn * sizeof(mt_loc);
+
+    // 1. which genomes the ranks hold: each at most once
+    std::vector<uint64_t> hold(G, 0);
+    for (uint32_t l = 0; l < Gs; l++) hold[genome_ids[l]]++;
+    if (allreduce(ctx, MT_XCHG_HOLDERS, hold.data(), G) != 0) return MT_EXCHANGE;
+    for (uint32_t g = 0; g < G; g++)
+        if (hold[g] > 1) return MT_EINVAL;
+
+    mt_part *q = nullptr;
+    int rc = mt_part_create(G, reads, n_bases, offsets, n_reads, device_ptrs, stream, &q);
+    if (rc) return rc;
+    Carver c;
+    const size_t o_ids = c.take<uint32_t>(std::max<uint32_t>(Gs, 1)), o_keep = c.take<uint8_t>(std::max<uint32_t>(Gs, 1));
+    const size_t o_tax = c.take<int32_t>(std::max<uint64_t>(n, 1)), o_nloc = c.take<uint8_t>(std::max<uint64_t>(n, 1));
+    const size_t o_mine = c.take<mt_loc>(std::max<uint64_t>(n * tn, 1));
+    const size_t o_all = c.take<mt_loc>(std::max<uint64_t>(n * tn * n_ranks, 1));
+    const size_t o_out = c.take<mt_loc>(std::max<uint64_t>(n * tn, 1)), o_a = c.take<double>(G);
+    unsigned char *ws = nullptr;
+    if ((rc = dalloc((void **)&ws, c.off + 256, s))) { mt_part_destroy(q); return rc; }
+    auto done = [&](int code) { dfree(ws, s); cudaStreamSynchronize(s); mt_part_destroy(q); return code; };
+    uint32_t *d_ids = (uint32_t *)(ws + o_ids);
+    uint8_t *d_keep = ws + o_keep;
+    int32_t *d_tax = (int32_t *)(ws + o_tax);
+    uint8_t *d_nloc = ws + o_nloc;
+    mt_loc *d_mine = (mt_loc *)(ws + o_mine), *d_all = (mt_loc *)(ws + o_all), *d_out = (mt_loc *)(ws + o_out);
+    double *d_a = (double *)(ws + o_a);
+
+    // 2. stage 1 over this rank's genomes; the hits summed over the ranks; the cutoff
+    if ((rc = mt_part_contain(q, shard, genome_ids, p->max_occ))) return done(rc);
+    std::vector<uint64_t> H(G);
+    if (!cuda_ok(cudaMemcpyAsync(H.data(), q->H, G * 8ull, cudaMemcpyDeviceToHost, s), "sharded hits") ||
+        !cuda_ok(cudaStreamSynchronize(s), "sharded hits"))
+        return done(MT_ECUDA);
+    if (allreduce(ctx, MT_XCHG_GENOME_HITS, H.data(), G) != 0) return done(MT_EXCHANGE);
+    if (!cuda_ok(cudaMemcpyAsync(q->H, H.data(), G * 8ull, cudaMemcpyHostToDevice, s), "sharded hits"))
+        return done(MT_ECUDA);
+    std::vector<uint8_t> keep(G);
+    if ((rc = mt_part_subset(q, p->cont_num, p->cont_den, keep.data(), genome_hits, nullptr, nullptr))) return done(rc);
+
+    // 3. stage 2 against this rank's kept genomes; locations in global ids
+    std::vector<uint8_t> keep_mine(std::max<uint32_t>(Gs, 1));
+    for (uint32_t l = 0; l < Gs; l++) keep_mine[l] = keep[genome_ids[l]];
+    if (!cuda_ok(cudaMemcpyAsync(d_keep, keep_mine.data(), Gs, cudaMemcpyHostToDevice, s), "sharded keep") ||
+        !cuda_ok(cudaMemcpyAsync(d_ids, genome_ids, Gs * 4ull, cudaMemcpyHostToDevice, s), "sharded ids"))
+        return done(MT_ECUDA);
+    rc = mt_classify_masked(shard, q->reads, q->n_bases, q->roff, n, p, 1, s, d_keep, d_tax, d_nloc, d_mine,
+                            nullptr, nullptr, stats);
+    if (rc) return done(rc);
+    if (n) {
+        k_part_ids<<<grid_for(n * tn), 256, 0, s>>>(n, tn, d_ids, nullptr, d_mine);
+        if (!cuda_ok(cudaGetLastError(), "k_part_ids")) return done(MT_ECUDA);
+    }
+
+    // 4. every rank's locations, merged by rank and decided on every rank
+    std::vector<unsigned char> mine(std::max<uint64_t>(per_rank, 1)), all(std::max<uint64_t>(per_rank * n_ranks, 1));
+    if ((per_rank && !cuda_ok(cudaMemcpyAsync(mine.data(), d_mine, per_rank, cudaMemcpyDeviceToHost, s), "sharded locs")) ||
+        !cuda_ok(cudaStreamSynchronize(s), "sharded locs"))
+        return done(MT_ECUDA);
+    if (allgather(ctx, MT_XCHG_LOCATIONS, mine.data(), per_rank, all.data()) != 0) return done(MT_EXCHANGE);
+    if (per_rank && !cuda_ok(cudaMemcpyAsync(d_all, all.data(), per_rank * n_ranks, cudaMemcpyHostToDevice, s), "sharded all"))
+        return done(MT_ECUDA);
+    if ((rc = merge_decide(d_all, n_ranks, q->roff, n, G, p, d_tax, d_nloc, d_out, d_a, s))) return done(rc);
+
+    const cudaMemcpyKind down = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if ((n && !cuda_ok(cudaMemcpyAsync(taxon, d_tax, n * 4, down, s), "sharded taxon")) ||
+        (n && nloc && !cuda_ok(cudaMemcpyAsync(nloc, d_nloc, n, down, s), "sharded nloc")) ||
+        (n && locs && !cuda_ok(cudaMemcpyAsync(locs, d_out, n * tn * sizeof(mt_loc), down, s), "sharded out")) ||
+        (abundance && !cuda_ok(cudaMemcpyAsync(abundance, d_a, G * 8ull, down, s), "sharded abundance")))
+        return done(MT_ECUDA);
+    return done(cuda_ok(cudaStreamSynchronize(s), "sharded") ? MT_OK : MT_ECUDA);
 }

@@ -85,6 +85,11 @@ def test_partitioned_query_argument_checks_without_gpu(mtlib):
     cp = mtlib.classify_params()
     assert L.mt_part_classify(None, None, None, 0, ctypes.byref(cp), None, None, None, None, None) == mtlib.MT_EINVAL
     L.mt_part_destroy(None)
+    ids = np.zeros(1, np.uint32)
+    assert L.mt_classify_genome_sharded(None, ctypes.c_void_p(ids.ctypes.data), 4, 2, ctypes.c_void_p(r.ctypes.data), 4,
+                                        ctypes.c_void_p(off.ctypes.data), 1, ctypes.byref(cp), 0, None,
+                                        mtlib.AllreduceFn(), mtlib.AllgatherFn(), None, None, None, None, None, None,
+                                        None) == mtlib.MT_EINVAL   # no shard, no exchange functions
     g = np.frombuffer(b"ACGT" * 10, np.uint8)
     goff = np.array([0, 40], np.uint64)
     ip = mtlib.IndexParams(15, 10, 1, 0)

@@ -132,3 +132,52 @@ def test_sharded_exchange_sums_over_two_gloo_ranks(tmp_path):
         assert x["hits"] == [10, 0, 2 ** 41 + 1, 7]
         assert x["uniq"] == [1, 2, 0, 6]
         assert x["multi"] == [0.75, 2e-17, 0.0, 5.0]
+
+
+def _gather_main(rank, world, port, out_dir):
+    """One rank of the genome-sharded exchange: the library's all-gather callback type wrapping
+    torch.distributed, called through its C function pointer as the library does, with the
+    holders sum that refuses overlapping shards."""
+    import ctypes
+
+    import numpy as np
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import paper_2311_02029_gb300 as mt
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    cb = mt.allgather_callback(mt.dist_allgather(), world)
+    call = mt.AllgatherFn(ctypes.cast(cb, ctypes.c_void_p).value)
+    locs = np.zeros(4, mt.LOC_DTYPE)          # this rank's per-read locations, 24 bytes each
+    locs["genome"] = np.arange(4) + 100 * rank
+    locs["wstart"] = -(rank + 1)
+    locs["dist"] = rank + 3
+    recv = np.zeros(4 * world, mt.LOC_DTYPE)
+    rcs = [call(None, mt.MT_XCHG_LOCATIONS, locs.ctypes.data, locs.nbytes, recv.ctypes.data)]
+    nothing = np.zeros(1, np.uint8)            # a batch with no reads still exchanges (0 bytes)
+    rcs.append(call(None, mt.MT_XCHG_LOCATIONS, nothing.ctypes.data, 0, nothing.ctypes.data))
+    hold = np.array([1, 0, 1, 0], np.uint64) if rank == 0 else np.array([0, 1, 1, 0], np.uint64)
+    ar = mt.AllreduceFn(ctypes.cast(mt.allreduce_callback(mt.dist_allreduce()), ctypes.c_void_p).value)
+    rcs.append(ar(None, mt.MT_XCHG_HOLDERS, hold.ctypes.data, len(hold)))
+
+    def broken(kind, send, recv):
+        raise RuntimeError("peer lost")
+    rcs.append(mt.allgather_callback(broken, world)(None, mt.MT_XCHG_LOCATIONS, locs.ctypes.data, locs.nbytes,
+                                                     recv.ctypes.data))
+    dist.barrier()
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, "g%d.json" % rank), "w") as f:
+        json.dump(dict(rcs=rcs, genome=recv["genome"].tolist(), wstart=recv["wstart"].tolist(),
+                       dist=recv["dist"].tolist(), hold=[int(x) for x in hold]), f)
+
+
+def test_genome_sharded_exchanges_over_two_gloo_ranks(tmp_path):
+    import torch.multiprocessing as tmp
+    tmp.spawn(_gather_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    res = [json.load(open(tmp_path / ("g%d.json" % r))) for r in range(2)]
+    for x in res:
+        assert x["rcs"] == [0, 0, 0, 1]
+        assert x["genome"] == [0, 1, 2, 3, 100, 101, 102, 103]      # rank order
+        assert x["wstart"] == [-1] * 4 + [-2] * 4
+        assert x["dist"] == [3] * 4 + [4] * 4
+        assert x["hold"] == [1, 1, 2, 0]                              # genome 2 held twice: refused
