@@ -191,14 +191,32 @@ __global__ void k_genome_min_count(const uint64_t *ref, const uint64_t *gword, c
     counts[c] = chunk_minimizers<0>(ref, gword[q.g], q.g, q.j0, q.j1, k, w, canonical, nullptr, nullptr);
 }
 
+// offs: the chunk's first output slot; counts (nullable): the number written, when offs are
+// upper-bound slots (one per window plus one) to be compacted afterwards
 __global__ void k_genome_min_write(const uint64_t *ref, const uint64_t *gword, const Chunk *ch,
                                    uint64_t n_chunks, uint32_t k, uint32_t w, uint32_t canonical,
-                                   const uint64_t *offs, uint64_t *codes, uint64_t *occs) {
+                                   const uint64_t *offs, uint64_t *codes, uint64_t *occs, uint64_t *counts) {
     uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_chunks) return;
     Chunk q = ch[c];
     uint64_t o = offs[c];
-    chunk_minimizers<1>(ref, gword[q.g], q.g, q.j0, q.j1, k, w, canonical, codes + o, occs + o);
+    const uint32_t n = chunk_minimizers<1>(ref, gword[q.g], q.g, q.j0, q.j1, k, w, canonical, codes + o, occs + o);
+    if (counts) counts[c] = n;
+}
+
+// packs every chunk's entries from its upper-bound slots to its place in chunk order (a warp
+// per chunk)
+__global__ void k_compact_chunks(uint64_t n_chunks, const uint64_t *ub, const uint64_t *cnt, const uint64_t *coff,
+                                 const uint64_t *code_in, const uint64_t *occ_in, uint64_t *code_out,
+                                 uint64_t *occ_out) {
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (warp >= n_chunks) return;
+    const uint64_t src = ub[warp], dst = coff[warp], n = cnt[warp];
+    for (uint64_t i = lane; i < n; i += 32) {
+        code_out[dst + i] = code_in[src + i];
+        occ_out[dst + i] = occ_in[src + i];
+    }
 }
 
 // ---- table insert -------------------------------------------------------------------------
@@ -417,7 +435,25 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, const uin
     if ((rc = dalloc((void **)&d_coff, (n_chunks + 1) * 8, s))) return rc;
     if (n_chunks) MT_CK(cudaMemcpyAsync(d_ch, chunks.data(), n_chunks * sizeof(Chunk), cudaMemcpyHostToDevice, s));
     MT_CK(cudaMemsetAsync(d_cnt, 0, (n_chunks + 1) * 8, s));
-    if (n_chunks) {
+    // One pass over the genomes when upper-bound staging (a window adds at most one position,
+    // a chunk at most its windows plus one) fits in a quarter of the free memory and 32 GB:
+    // chunks write at upper-bound slots and record their counts, then a compaction packs them
+    // in chunk order. Otherwise the minimizers are found twice: counted, then written.
+    std::vector<uint64_t> ub(n_chunks + 1, 0);
+    for (uint64_t c = 0; c < n_chunks; c++) ub[c + 1] = ub[c] + (chunks[c].j1 - chunks[c].j0) + 1;
+    size_t free_b = 0, total_b = 0;
+    MT_CK(cudaMemGetInfo(&free_b, &total_b));
+    const bool one_pass = n_chunks && ub[n_chunks] * 16 <= std::min<uint64_t>(free_b / 4, 32ull << 30);
+    uint64_t *d_ub = nullptr, *d_ub_code = nullptr, *d_ub_occ = nullptr;
+    if (one_pass) {
+        if ((rc = dalloc((void **)&d_ub, (n_chunks + 1) * 8, s))) return rc;
+        if ((rc = dalloc((void **)&d_ub_code, ub[n_chunks] * 8, s))) return rc;
+        if ((rc = dalloc((void **)&d_ub_occ, ub[n_chunks] * 8, s))) return rc;
+        MT_CK(cudaMemcpyAsync(d_ub, ub.data(), (n_chunks + 1) * 8, cudaMemcpyHostToDevice, s));
+        k_genome_min_write<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(
+            ix->d_ref, ix->d_gword, d_ch, n_chunks, p->k, p->w, ix->canonical, d_ub, d_ub_code, d_ub_occ, d_cnt);
+        MT_CK(cudaGetLastError());
+    } else if (n_chunks) {
         k_genome_min_count<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(
             ix->d_ref, ix->d_gword, d_ch, n_chunks, p->k, p->w, ix->canonical, d_cnt);
         MT_CK(cudaGetLastError());
@@ -439,10 +475,15 @@ static int build_impl(const uint8_t *genomes, const uint64_t *offsets, const uin
     if ((rc = dalloc((void **)&d_code[1], nb, s))) return rc;
     if ((rc = dalloc((void **)&d_val[0], nb, s))) return rc;
     MT_CK(cudaMalloc((void **)&d_val[1], nb));   // becomes the resident occurrence array
-    if (n_chunks) {
+    if (one_pass) {
+        k_compact_chunks<<<(unsigned)((n_chunks * 32 + 255) / 256), 256, 0, s>>>(
+            n_chunks, d_ub, d_cnt, d_coff, d_ub_code, d_ub_occ, d_code[0], d_val[0]);
+        MT_CK(cudaGetLastError());
+        dfree(d_ub, s); dfree(d_ub_code, s); dfree(d_ub_occ, s);
+    } else if (n_chunks) {
         k_genome_min_write<<<(unsigned)((n_chunks + 127) / 128), 128, 0, s>>>(
             ix->d_ref, ix->d_gword, d_ch, n_chunks, p->k, p->w, ix->canonical, d_coff,
-            d_code[0], d_val[0]);
+            d_code[0], d_val[0], nullptr);
         MT_CK(cudaGetLastError());
     }
     dfree(d_ch, s); dfree(d_cnt, s); dfree(d_coff, s);
