@@ -35,6 +35,10 @@ METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact)
 # index is fixed, so traffic grows in proportion to the reads. None whenever the kernel has
 # changed since the last capture.
 SEED_DRAM_BYTES_PER_READ = (7.053661e9 + 0.250544e9) / 2e6
+# Warp instructions per read of the seeding kernel (smsp__inst_executed.sum of the same capture,
+# 3.4526e9 on 2e6 reads); None whenever the kernel has changed since the last capture. The
+# kernel is bound by instruction issue, not DRAM: the issue roofline below uses it.
+SEED_WARP_INST_PER_READ = 3452561196 / 2e6
 WORKLOAD = ("medium: 200 genomes x 2 Mb (20 clades x 10, 1-10% divergence), k21 w11 canonical, "
             "1e7 reads x 150 bp (both strands, 0.5% subst + 0.05% indel, 5% random), E=8, min_seeds 3, top 3")
 
@@ -503,11 +507,23 @@ def run_ours(args):
     seed_requests = st["n_minimizers"] + st["n_ext_occ"] * 8 / 32.0
     gather_gps = gather_ceiling(torch)
     achieved = seed_bytes / (st["ms_seed"] / 1000.0) / 1e9
+    # instruction issue: one warp instruction per cycle per scheduler, 4 schedulers per SM, at
+    # the SM clock sampled during the timed region (the maximum clock when none was sampled)
+    issue = None
+    if SEED_WARP_INST_PER_READ:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        peak_issue = sms * 4 * mhz * 1e6 / 1e9
+        got_issue = SEED_WARP_INST_PER_READ * n_reads / (st["ms_seed"] / 1000.0) / 1e9
+        issue = {"achieved": got_issue, "peak": peak_issue, "unit": "G warp instructions/s",
+                 "frac": got_issue / peak_issue, "warp_instructions_per_read": SEED_WARP_INST_PER_READ,
+                 "peak_kind": "%d SMs x 4 schedulers x 1 instruction/cycle x %.0f MHz (sampled SM clock)" % (sms, mhz)}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (SEED_DRAM_BYTES_PER_READ * n_reads if SEED_DRAM_BYTES_PER_READ else None),
                 "kernel": "k_seed",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": seed_bytes, "ms_per_launch": st["ms_seed"],
+                "issue": issue,
                 "random_access": {"achieved": seed_requests / (st["ms_seed"] / 1000.0) / 1e9,
                                   "peak": gather_gps, "unit": "G random requests/s",
                                   "frac": seed_requests / (st["ms_seed"] / 1000.0) / 1e9 / gather_gps,
