@@ -42,7 +42,7 @@ static constexpr uint32_t RDW = MT_MAX_READ_LEN / 32 + 2;
 static constexpr uint32_t CSTORE = 8;                     // locations stored per read
 static constexpr uint32_t QOVF = 0xFFFFFFFFu;
 static constexpr uint32_t SMEM_HIST_MAX = 4096;
-static constexpr uint32_t MULTI_UNROLL = 4;     // key-filter loads in flight per lane (several indexes)
+static constexpr uint32_t MULTI_UNROLL = 2;     // key-filter loads in flight per lane (several indexes)
 static constexpr uint32_t MULTI_MAX = 4096;     // indexes counted in one pass (exact pair / n_bv)           // genomes counted in shared memory
 static constexpr int FB_CTAS = 16;
 static constexpr int FB_THREADS = 256;
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             n_mins += nm;
             if (MULTI) {
                 // (minimizer, batch) pairs: the batches' key filters (small, in L2) are tested
-                // four pairs a lane at a time, so four loads are in flight; the pairs that pass
+                // MULTI_UNROLL pairs a lane at a time (their loads in flight together); the pairs that pass
                 // (about one batch per minimizer) are queued in the idle match buffer and
                 // probed one a lane, matches counted into the batch's genome counters.
                 const uint32_t B = A.n_bv, np = nm * B;
