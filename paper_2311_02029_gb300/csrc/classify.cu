@@ -1403,6 +1403,7 @@ struct EnqueueCtx {
     uint32_t n_chunks;
     const uint64_t *chunk_r;
     const cudaEvent_t *chunk_ev;
+    bool capturing;           // the enqueue is being captured: chunk events are external waits
 };
 
 // Replaces the G-vector at `dev` with its sum over the ranks of a sharded batch (a no-op for an
@@ -1473,7 +1474,7 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         int rc = MT_OK;
         if (c.n_chunks) {   // seed each chunk of reads as soon as its bytes have arrived
             for (uint32_t i = 0; i < c.n_chunks && !rc; i++) {
-                MT_CK(cudaStreamWaitEvent(s, c.chunk_ev[i], 0));
+                MT_CK(cudaStreamWaitEvent(s, c.chunk_ev[i], c.capturing ? cudaEventWaitExternal : 0));
                 rc = seed(c.chunk_r[i], c.chunk_r[i + 1]);
             }
             c.launches += c.n_chunks - 1;
@@ -2016,6 +2017,16 @@ struct mt_plan {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
     uint64_t calls = 0, launches = 0;
+    // Host batches go up in chunks of reads on a copy stream, each seeded as it lands: chunk i
+    // holds reads [chunk_r[i], chunk_r[i+1]) of the capacity (fixed, so one graph serves
+    // every batch); the graph waits on chunk_ev[i], recorded each call after the chunk's copy
+    // (or at once for device inputs).
+    static constexpr uint32_t MAX_CHUNKS = 8;
+    uint32_t n_chunks = 1;
+    uint64_t chunk_r[MAX_CHUNKS + 1] = {};
+    cudaEvent_t chunk_ev[MAX_CHUNKS] = {};
+    cudaEvent_t ready = nullptr;
+    cudaStream_t copy_stream = nullptr;
 };
 
 extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, uint64_t max_reads,
@@ -2048,6 +2059,19 @@ extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, u
         delete pl;
         return MT_ENOMEM;
     }
+    // one chunk per 2^17 reads of capacity, at most MAX_CHUNKS (each chunk is one more seeding
+    // launch, whose tail wave costs a little even when the reads are already on the device)
+    pl->n_chunks = (uint32_t)std::min<uint64_t>(mt_plan::MAX_CHUNKS, std::max<uint64_t>(1, max_reads >> 17));
+    for (uint32_t i = 0; i <= pl->n_chunks; i++) pl->chunk_r[i] = max_reads * i / pl->n_chunks;
+    bool ok = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&pl->ready, cudaEventDisableTiming) == cudaSuccess;
+    for (uint32_t i = 0; ok && i < pl->n_chunks; i++)
+        ok = cudaEventCreateWithFlags(&pl->chunk_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cuda_ok(cudaGetLastError(), "plan streams");
+        mt_plan_destroy(pl);
+        return MT_ECUDA;
+    }
     *out = pl;
     return MT_OK;
 }
@@ -2067,8 +2091,15 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
     if (stats) memset(stats, 0, sizeof(*stats));
     uint64_t off0 = 0;
     // reads with bad offsets or above the plan's read length are flagged by the seeding kernel
-    // (MT_EINVAL after the call), so host offsets are not scanned here
+    // (MT_EINVAL after the call), so host offsets are not scanned here, except the chunk
+    // boundaries, which bound the copies (non-decreasing offsets keep a read inside its chunk)
     if (host_io) {
+        uint64_t prev = n_reads ? offsets[0] : 0;
+        for (uint32_t i = 0; n_reads && i <= pl->n_chunks; i++) {
+            const uint64_t o = offsets[std::min(pl->chunk_r[i], n_reads)];
+            if (o < prev || o > n_bases) return MT_EINVAL;
+            prev = o;
+        }
         if (n_reads) off0 = offsets[0];
     } else if (n_reads) {
         MT_CK(cudaMemcpyAsync(&pl->h_ctr->stat[0], offsets, 8, cudaMemcpyDeviceToHost, s));
@@ -2085,11 +2116,27 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
         io.taxon = (int32_t *)P(L.taxon);
         io.nloc = (uint8_t *)P(L.nloc);
         io.locs = locs ? (mt_loc *)P(L.locs) : nullptr;
-        if (n_bases) MT_CK(cudaMemcpyAsync((void *)io.reads, reads, n_bases, cudaMemcpyHostToDevice, s));
         MT_CK(cudaMemcpyAsync((void *)io.roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
     }
     io.vec_ok = ((uintptr_t)io.reads & 15u) == 0;
     MT_CK(cudaMemcpyAsync(P(L.io), pl->h_io, sizeof(IoBlock), cudaMemcpyHostToDevice, s));
+    if (host_io) {   // the reads' bytes, chunk by chunk, after what s has queued
+        // (a single chunk goes up on s itself: nothing to overlap)
+        cudaStream_t cs = pl->n_chunks > 1 ? pl->copy_stream : s;
+        if (cs != s) {
+            MT_CK(cudaEventRecord(pl->ready, s));
+            MT_CK(cudaStreamWaitEvent(cs, pl->ready, 0));
+        }
+        for (uint32_t i = 0; i < pl->n_chunks; i++) {
+            const uint64_t rb = std::min(pl->chunk_r[i], n_reads), re = std::min(pl->chunk_r[i + 1], n_reads);
+            if (re > rb && offsets[re] > offsets[rb])
+                MT_CK(cudaMemcpyAsync((uint8_t *)io.reads + offsets[rb], reads + offsets[rb], offsets[re] - offsets[rb],
+                                      cudaMemcpyHostToDevice, cs));
+            MT_CK(cudaEventRecord(pl->chunk_ev[i], cs));
+        }
+    } else {
+        for (uint32_t i = 0; i < pl->n_chunks; i++) MT_CK(cudaEventRecord(pl->chunk_ev[i], s));
+    }
 
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (stats) {
@@ -2098,6 +2145,9 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
         MT_CK(cudaEventRecord(ev[0], s));
     }
     EnqueueCtx ctx{pl->ix, &pl->p, &L, pl->ws, pl->cap_reads, pl->max_len, pl->maxE, true, nullptr, 0};
+    ctx.n_chunks = pl->n_chunks;
+    ctx.chunk_r = pl->chunk_r;
+    ctx.chunk_ev = pl->chunk_ev;
     int rc = MT_OK;
     if (pl->calls == 0) {
         // the first call runs directly (it may autotune the approximation kernel)
@@ -2108,6 +2158,7 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
             // capture on the plan's own stream (the caller's may be the legacy default
             // stream, which cannot be captured); the graph is then launched on the caller's
             ctx.allow_tune = false;
+            ctx.capturing = true;
             if (!pl->cap_stream) MT_CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
             MT_CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
             rc = enqueue_classify(ctx, pl->cap_stream);
@@ -2150,6 +2201,13 @@ extern "C" void mt_plan_destroy(mt_plan *pl) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
+    if (pl->copy_stream) {
+        cudaStreamSynchronize(pl->copy_stream);
+        cudaStreamDestroy(pl->copy_stream);
+    }
+    for (uint32_t i = 0; i < mt_plan::MAX_CHUNKS; i++)
+        if (pl->chunk_ev[i]) cudaEventDestroy(pl->chunk_ev[i]);
+    if (pl->ready) cudaEventDestroy(pl->ready);
     cudaFree(pl->ws);
     cudaFreeHost(pl->h_io);
     cudaFreeHost(pl->h_ctr);

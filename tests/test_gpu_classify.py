@@ -309,3 +309,36 @@ def test_host_batch_uploaded_in_chunks(mt):
     oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
     ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=16)
     compare_classify(host, ref)
+
+
+def test_plan_with_chunked_uploads_matches_oracle(mt):
+    """A plan of 300,000 reads uploads host batches in chunks of reads (2 here), each seeded as it lands,
+    inside the captured graph: batches spanning several chunks, device batches through the
+    same graph, and an offset at a chunk boundary past the bytes refused before any copy."""
+    import torch
+    c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=250_000, seed=97)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"], threads=8)
+    prm = _params(c)
+    plan = mt.Plan(ix, max_reads=300_000, max_bases=300_000 * 150, max_read_len=150, **prm)
+    cuts = [(0, 250_000), (20_000, 120_000), (100_000, 170_001), (5, 5_005), (0, 250_000)]
+    for i, (a, b) in enumerate(cuts):
+        seq = r.seq[int(r.offsets[a]):int(r.offsets[b])]
+        off = (r.offsets[a:b + 1] - r.offsets[a]).astype(np.uint64)
+        ref = oracle.classify(oix, seq, off, oracle_params(prm), threads=16)
+        if i == 1:
+            out = plan.classify(torch.from_numpy(seq.copy()).cuda(), torch.from_numpy(off.astype(np.int64)).cuda())
+        else:
+            out = plan.classify(seq, off)
+        compare_classify(out, ref)
+    seq = r.seq[:int(r.offsets[200_000])]
+    off = r.offsets[:200_001].copy()
+    off[150_000:] += np.uint64(10 ** 9)          # reads past the bytes from the second chunk on
+    with pytest.raises(mt.MtError) as e:
+        plan.classify(seq, off)
+    assert e.value.status == mt.MT_EINVAL
+    ok = plan.classify(r.seq[:300], np.array([0, 150, 300], np.uint64))   # still usable
+    assert len(ok["taxon"]) == 2
+    plan.close()
