@@ -4,11 +4,15 @@
 // Stage 1 runs batch by batch with each batch's own index (the counting seeding kernel of
 // mt_containment), or for all resident batches at once in one pass of that kernel that finds
 // each read's minimizers once and looks them up in every batch's table; a genome keeps the
-// highest count any batch gave it (one atomicMax per genome slot). The normalised cutoff then runs over the whole database, and stages 2-3 run
-// against the subset index of the kept genomes (mt_classify_masked, every subset genome
-// kept); the subset's genome ids are mapped back to global ids on the device. Between calls
-// the query holds only the reads and n_genomes-sized vectors, so database batches can pass
-// through device memory one at a time.
+// highest count any batch gave it (one atomicMax per genome slot). The normalised cutoff then
+// runs over the whole database, and stages 2-3 run against the subset index of the kept
+// genomes (mt_classify_masked, every subset genome kept); the subset's genome ids are mapped
+// back to global ids on the device. Between calls the query holds only the reads and
+// n_genomes-sized vectors, so database batches can pass through device memory one at a time.
+//
+// Genome shards over ranks (mt_classify_genome_sharded, at the end of this file) reuse the
+// query: each rank counts and maps against its own shard, and every rank merges all ranks'
+// per-read locations by rank and decides them (merge_decide).
 #include <algorithm>
 #include <cstring>
 #include <vector>
