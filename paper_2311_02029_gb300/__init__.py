@@ -778,14 +778,31 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, reads, offsets) -> int:
+    def submit(self, reads, offsets, out=None) -> int:
+        """Queues one batch; returns its request id. ``out`` may hold caller-owned output arrays
+        (taxon, nloc, locs, genome_hits, abundance) of at least this batch's size, e.g. reused
+        from an earlier request, which avoids faulting in fresh pages for every request."""
         r = _host_u8(reads)
         off = _host_u64(offsets)
         n = len(off) - 1
         G = self.ix.n_genomes
-        out = dict(taxon=np.empty(n, np.int32), nloc=np.empty(n, np.uint8),
-                   locs=np.empty((n, self.p.top_n), LOC_DTYPE), genome_hits=np.empty(G, np.uint64),
-                   abundance=np.empty(G, np.float64))
+        if out is None:
+            out = dict(taxon=np.empty(n, np.int32), nloc=np.empty(n, np.uint8),
+                       locs=np.empty((n, self.p.top_n), LOC_DTYPE), genome_hits=np.empty(G, np.uint64),
+                       abundance=np.empty(G, np.float64))
+        else:
+            if (len(out["taxon"]) < n or len(out["nloc"]) < n or len(out["locs"]) < n
+                    or len(out["genome_hits"]) < G or len(out["abundance"]) < G):
+                raise ValueError("output arrays smaller than the batch")
+            out = dict(taxon=out["taxon"][:n], nloc=out["nloc"][:n], locs=out["locs"][:n],
+                       genome_hits=out["genome_hits"][:G], abundance=out["abundance"][:G])
+            for k, dt in (("taxon", np.int32), ("nloc", np.uint8), ("genome_hits", np.uint64),
+                          ("abundance", np.float64)):
+                if out[k].dtype != dt or not out[k].flags["C_CONTIGUOUS"]:
+                    raise ValueError("output %s must be contiguous %s" % (k, np.dtype(dt).name))
+            if (out["locs"].dtype != LOC_DTYPE or not out["locs"].flags["C_CONTIGUOUS"]
+                    or out["locs"].shape[1:] != (self.p.top_n,)):
+                raise ValueError("output locs must be contiguous (n, top_n) locations")
         rid = ctypes.c_uint64()
         _check(lib().mt_server_submit(self._h, _ptr(r), len(r), _ptr(off), n, _ptr(out["taxon"]),
                                       _ptr(out["nloc"]), _ptr(out["locs"]), _ptr(out["genome_hits"]),

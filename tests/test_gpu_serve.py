@@ -103,3 +103,28 @@ def test_cancel_and_bounded_poll(mt, work):
         assert rc == mt.MT_OK
     assert srv.cancel(ids[0]) == mt.MT_EBUSY              # already done
     srv.close()
+
+
+def test_requests_into_reused_output_arrays(mt, work):
+    """Caller-owned output arrays, larger than the batch and reused by later requests, hold each
+    request's results exactly; arrays too small are refused before anything is queued."""
+    import torch
+    c, g, r, ix, prm = work
+    free, _ = torch.cuda.mem_get_info()
+    srv = mt.Server(ix, hbm_budget=free // 3, max_slots=2, **prm)
+    cap, G = 6000, g.n
+    buf = dict(taxon=np.full(cap, 7, np.int32), nloc=np.full(cap, 9, np.uint8),
+               locs=np.zeros((cap, 3), mt.LOC_DTYPE), genome_hits=np.zeros(G, np.uint64),
+               abundance=np.zeros(G, np.float64))
+    for a, b in ((0, 5000), (7000, 7100), (100, 6100)):
+        seq, off = _batch(r, a, b)
+        ref = mt.classify(ix, seq, off, **prm)
+        rid = srv.submit(seq, off, out=buf)
+        rc, lat, out = srv.poll(rid, 60_000)
+        assert rc == mt.MT_OK and len(out["taxon"]) == b - a
+        _same(out, ref)
+        assert out["taxon"].base is buf["taxon"] or np.shares_memory(out["taxon"], buf["taxon"])
+    seq, off = _batch(r, 0, cap + 1)
+    with pytest.raises(ValueError):
+        srv.submit(seq, off, out=buf)
+    srv.close()
