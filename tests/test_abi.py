@@ -142,3 +142,18 @@ def test_load_index_refuses_non_index_files_without_gpu(mtlib, tmp_path):
     assert L.mt_load_index(str(p).encode(), None, ctypes.byref(out)) == mtlib.MT_EIO
     assert not out.value
     assert L.mt_load_index(None, None, ctypes.byref(out)) == mtlib.MT_EINVAL
+
+
+def test_gather_genomes_without_gpu(mtlib):
+    """The binding's host gather of genome bytes (inputs of batch and subset indexes): ids in
+    any order, repeats, empty genomes, no ids."""
+    rng = np.random.default_rng(5)
+    lens = rng.integers(0, 40, 12)
+    lens[3] = 0
+    seq = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, int(lens.sum()))].copy()
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    for ids in ([5, 1, 3, 3, 11], [0], [], list(range(12))[::-1]):
+        s, o = mtlib.gather_genomes(seq, off, ids)
+        assert o.tolist() == [0] + np.cumsum([int(lens[i]) for i in ids]).tolist()
+        exp = b"".join(seq[int(off[i]):int(off[i + 1])].tobytes() for i in ids)
+        assert s.tobytes() == exp
