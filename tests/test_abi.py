@@ -157,3 +157,20 @@ def test_gather_genomes_without_gpu(mtlib):
         assert o.tolist() == [0] + np.cumsum([int(lens[i]) for i in ids]).tolist()
         exp = b"".join(seq[int(off[i]):int(off[i + 1])].tobytes() for i in ids)
         assert s.tobytes() == exp
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/mt.h compiles as strict C99 (the boundary takes no C++ or torch types) and links
+    against libmt.so from a C program."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "mt.h"\n#include <stdio.h>\nint main(void) {\n'
+                   '    mt_index *ix = 0;\n    printf("%d %s\\n", mt_version(), mt_strerror(MT_EINVAL));\n'
+                   '    return mt_build_index(0, 0, 0, 0, 0, &ix) == MT_EINVAL && ix == 0 ? 0 : 1;\n}\n')
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), "-fsyntax-only", str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
