@@ -159,7 +159,7 @@ def test_gather_genomes_without_gpu(mtlib):
         assert s.tobytes() == exp
 
 
-def test_header_is_plain_c(tmp_path):
+def test_header_is_plain_c(mtlib, tmp_path):
     """include/mt.h compiles as strict C99 (the boundary takes no C++ or torch types) and links
     against libmt.so from a C program."""
     import shutil
@@ -171,6 +171,11 @@ def test_header_is_plain_c(tmp_path):
     src.write_text('#include "mt.h"\n#include <stdio.h>\nint main(void) {\n'
                    '    mt_index *ix = 0;\n    printf("%d %s\\n", mt_version(), mt_strerror(MT_EINVAL));\n'
                    '    return mt_build_index(0, 0, 0, 0, 0, &ix) == MT_EINVAL && ix == 0 ? 0 : 1;\n}\n')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(mtlib.LIB_PATH)
     r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
-                        os.path.join(ROOT, "include"), "-fsyntax-only", str(src)], capture_output=True, text=True)
+                        os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lmt",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)   # argument checks only
+    assert r.returncode == 0 and r.stdout.split()[0] == str(mtlib.lib().mt_version()), (r.stdout, r.stderr)
