@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -87,7 +88,9 @@ class Clocks:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu)
+        # the raw samples, summarised into the JSON line (MT_CLOCKS_DIR keeps them elsewhere)
+        self.path = os.path.join(os.environ.get("MT_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "mt_bench_clocks_%d_%d.csv" % (gpu, os.getpid()))
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
