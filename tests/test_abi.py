@@ -179,3 +179,33 @@ def test_header_is_plain_c(mtlib, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)   # argument checks only
     assert r.returncode == 0 and r.stdout.split()[0] == str(mtlib.lib().mt_version()), (r.stdout, r.stderr)
+
+
+def test_every_entry_point_refuses_null_arguments_without_gpu(mtlib):
+    """Missing or out-of-range arguments come back as MT_EINVAL (0 for the size query) from
+    every entry point, before any device work; no call aborts the process."""
+    L = mtlib.lib()
+    E = mtlib.MT_EINVAL
+    cp = mtlib.classify_params()
+    st = mtlib.Stats()
+    out = ctypes.c_void_p()
+    d = ctypes.c_double()
+    rid = ctypes.c_uint64()
+    buf = np.zeros(64, np.uint64)
+    p = ctypes.c_void_p(buf.ctypes.data)
+    assert L.mt_classify(None, p, 8, p, 1, ctypes.byref(cp), 0, None, p, p, p, p, p, ctypes.byref(st)) == E
+    assert L.mt_classify_masked(None, p, 8, p, 1, ctypes.byref(cp), 0, None, None, p, p, p, p, p,
+                                ctypes.byref(st)) == E
+    assert L.mt_containment(None, p, 8, p, 1, 16, 1, 10000, 0, None, p, p) == E
+    assert L.mt_classify_workspace_bytes(None, 8, 1, 150, ctypes.byref(cp)) == 0
+    assert L.mt_plan_create(None, ctypes.byref(cp), 10, 1000, 150, ctypes.byref(out)) == E and not out.value
+    assert L.mt_plan_classify(None, p, 8, p, 1, 0, None, p, p, p, p, p, ctypes.byref(st)) == E
+    assert L.mt_pack_seqs(None, p, 1, p, None) == E
+    assert L.mt_eda_batch_noalloc(p, p, 1, p, p, p, p, 1, 99, None, p) == E            # no such form
+    assert L.mt_eda_batch_noalloc(p, p, 1, p, p, p, p, 1 << 40, 0, None, p) == E       # too many pairs
+    assert L.mt_save_index(None, b"/nonexistent/x.idx", None) == E
+    assert L.mt_load_index(None, None, ctypes.byref(out)) == E
+    assert L.mt_index_get_info(None, None) == E
+    assert L.mt_server_submit(None, p, 8, p, 1, p, p, p, p, p, ctypes.byref(rid)) == E
+    assert L.mt_server_poll(None, 1, 0, ctypes.byref(d)) == E
+    assert L.mt_profile_rollup(None, 2, None, None, 0, None) == E
