@@ -41,9 +41,8 @@ static constexpr uint32_t HCAP = 256;                     // seed matches held p
 static constexpr uint32_t RDW = MT_MAX_READ_LEN / 32 + 2;
 static constexpr uint32_t CSTORE = 8;                     // locations stored per read
 static constexpr uint32_t QOVF = 0xFFFFFFFFu;
-static constexpr uint32_t SMEM_HIST_MAX = 4096;
+static constexpr uint32_t SMEM_HIST_MAX = 4096;           // genomes counted in shared memory
 static constexpr uint32_t MULTI_UNROLL = 2;     // key-filter loads in flight per lane (several indexes)
-static constexpr uint32_t MULTI_MAX = 4096;     // indexes counted in one pass (exact pair / n_bv)           // genomes counted in shared memory
 static constexpr int FB_CTAS = 16;
 static constexpr int FB_THREADS = 256;
 
@@ -1877,7 +1876,7 @@ int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const 
                       const uint64_t *offsets, uint64_t n_reads, uint32_t max_occ, uint64_t *hits, cudaStream_t s) {
     if (!n_batches) return MT_OK;
     if (!batches || !batches[0] || !hits || !offsets || (!reads && n_bases) || max_occ > MT_MAX_OCC_LIMIT ||
-        n_batches > MULTI_MAX)
+        n_batches > MULTI_MAX_INDEXES)
         return MT_EINVAL;
     const mt_index *b0 = batches[0];
     std::vector<BatchView> hv(n_batches);

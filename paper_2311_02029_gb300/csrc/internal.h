@@ -80,8 +80,11 @@ int launch_pack_seqs(const uint8_t *seq, const uint64_t *off, uint64_t n, uint64
                      uint64_t total_words, uint32_t *err, cudaStream_t s);
 // (Re)builds the index's key filter from its table (after a build or a load).
 int build_key_filter(mt_index *ix, cudaStream_t s);
-// Seed hits of several indexes of one (k, w, canonical, compression) in one pass over device
-// reads; hits (device) gets the indexes' genome counters one after another.
+// Seed hits of several indexes (at most MULTI_MAX_INDEXES, so that a (minimizer, index) pair
+// number divided by their count stays exact with a 32-bit multiply) of one (k, w, canonical,
+// compression) in one pass over device reads; hits (device) gets the indexes' genome counters
+// one after another.
+constexpr uint32_t MULTI_MAX_INDEXES = 4096;
 int contain_multi(const mt_index *const *batches, uint32_t n_batches, const uint8_t *reads, uint64_t n_bases,
                   const uint64_t *offsets, uint64_t n_reads, uint32_t max_occ, uint64_t *hits, cudaStream_t s);
 // Per-read location lists of R genome shards (device, rank order) merged by rank and decided:

@@ -180,8 +180,13 @@ extern "C" int mt_part_contain_batches(mt_part *q, const mt_index *const *batche
     auto done = [&](int code) { dfree(ws, q->s); cudaStreamSynchronize(q->s); return code; };
     if (!cuda_ok(cudaMemcpyAsync(d_ids, ids.data(), T * 4, cudaMemcpyHostToDevice, q->s), "part ids"))
         return done(MT_ECUDA);
-    rc = contain_multi(batches, n_batches, q->reads, q->n_bases, q->roff, q->n_reads, max_occ, hits, q->s);
-    if (rc) return done(rc);
+    // one pass per MULTI_MAX_INDEXES batches
+    for (uint32_t b0 = 0, base = 0; b0 < n_batches; b0 += MULTI_MAX_INDEXES) {
+        const uint32_t nb = std::min(n_batches - b0, MULTI_MAX_INDEXES);
+        rc = contain_multi(batches + b0, nb, q->reads, q->n_bases, q->roff, q->n_reads, max_occ, hits + base, q->s);
+        if (rc) return done(rc);
+        for (uint32_t b = b0; b < b0 + nb; b++) base += batches[b]->G;
+    }
     k_part_max<<<grid_for(T), 256, 0, q->s>>>((const unsigned long long *)hits, d_ids, (uint32_t)T, q->H);
     if (!cuda_ok(cudaGetLastError(), "k_part_max")) return done(MT_ECUDA);
     q->have_subset = false;
