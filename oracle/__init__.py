@@ -11,13 +11,15 @@ window minima, brute-force seed enumeration per genome, a hand-worked SneakySnak
 the E = 0 Hamming reduction, an exact dynamic-programming restatement of the greedy walk,
 upper bounds by per-diagonal Hamming distance and by banded edit distance (no false
 reject), a lower bound by all-obstacle columns, planted-truth mapping of error-free reads,
-and hand-computed abundance splits; for a database cut into batches, reduction to the
-single-index pipeline when no key reaches the repeat filter, highest-not-summed counts of a
-genome held by several batches, and brute-force per-batch repeat filtering; for genome
-shards on separate devices, reduction to the single-index pipeline and a hand-worked merge by
-rank with a unique read whose best locations share one genome. Parity unpinned (defined readings with no external
-check): the location clustering rule, rank tie-breaks, the max_occ repeat filter and the
-multi-read split -- the CUDA path must still agree with them bit-exactly.
+a location spanning exactly E diagonals, a hand-worked rank order of equal-seed locations
+(strand, then first diagonal), brute-force mapping locations with the repeat filter at the
+exact occurrence count, and hand-computed abundance splits; for a database cut into batches,
+reduction to the single-index pipeline when no key reaches the repeat filter,
+highest-not-summed counts of a genome held by several batches, and brute-force per-batch
+repeat filtering; for genome shards on separate devices, reduction to the single-index
+pipeline and a hand-worked merge by rank with a unique read whose best locations share one
+genome. Every reading the oracle takes (mixer, leftmost-minimum tie, location clustering,
+rank tie-breaks, repeat filter, window edges, multi-read split) has such a pin.
 """
 from __future__ import annotations
 

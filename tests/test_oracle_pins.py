@@ -607,3 +607,114 @@ def test_threaded_index_build_is_identical(oracle_lib):
     assert np.array_equal(ra["locs"], rb["locs"])
     for code in np.unique(oracle.minimizers(g.genome(3), c["k"], c["w"], 1)[0])[:200]:
         assert [x.tolist() for x in a.lookup(int(code))] == [x.tolist() for x in b.lookup(int(code))]
+
+
+def test_rank_ties_break_by_strand_then_first_diagonal(oracle_lib):
+    """Hand-worked ranking of equal-seed locations (Methods, "Empirically Determined
+    Parameters": the top three locations by seed count). One genome holds an exact copy of
+    the read S at p1, its reverse complement at p2 and S again at p3, with p1 < p2 < p3. With
+    canonical seeds every read minimizer matches all three copies, so the three locations
+    tie on seeds and on genome. Written by hand from the ranking reading (seeds descending,
+    then genome, strand and first diagonal ascending), the order is (+, p1), (+, p3), (-, p2):
+    strand before diagonal, both ascending. A second genome holding one forward copy ranks
+    after every location of genome 0, whatever its strand."""
+    rng = np.random.default_rng(41)
+    k, w, E, n = 15, 10, 4, 150
+    S = "".join(rng.choice(list("ACGT"), n))
+    rcS = S[::-1].translate(_RC)
+    f = _rand_genomes(rng, [300, 400, 500, 300, 350, 250])
+    g0 = f[0] + S + f[1] + rcS + f[2] + S + f[3]
+    p1 = len(f[0])
+    p2 = p1 + n + len(f[1])
+    p3 = p2 + n + len(f[2])
+    g1 = f[4] + S + f[5]
+    q1 = len(f[4])
+    seq, off = _pack([g0, g1])
+    ix = oracle.Index(seq, off, k, w, 1)
+    nm = len(brute_minimizers(S, k, w, 1))
+    assert nm >= 3
+    rs, ro = _pack([S])
+    res = oracle.classify(ix, rs, ro, oracle.params(e_abs=E, e_permille=0, min_seeds=2, top_n=3))
+    got = [(int(L["genome"]), int(L["strand"]), int(L["wstart"]), int(L["seeds"]), int(L["dist"]))
+           for L in res["locs"][0]]
+    assert got == [(0, 0, p1 - E, nm, 0), (0, 0, p3 - E, nm, 0), (0, 1, p2 - E, nm, 0)]
+    # with room for all four, genome 1's forward copy comes last
+    res = oracle.classify(ix, rs, ro, oracle.params(e_abs=E, e_permille=0, min_seeds=2, top_n=4))
+    assert [(int(L["genome"]), int(L["strand"]), int(L["wstart"])) for L in res["locs"][0]] == \
+        [(0, 0, p1 - E), (0, 0, p3 - E), (0, 1, p2 - E), (1, 0, q1 - E)]
+    # the reverse-complemented read: the rc copy is now the forward-strand location
+    rs, ro = _pack([rcS])
+    res = oracle.classify(ix, rs, ro, oracle.params(e_abs=E, e_permille=0, min_seeds=2, top_n=3))
+    assert [(int(L["genome"]), int(L["strand"]), int(L["wstart"])) for L in res["locs"][0]] == \
+        [(0, 0, p2 - E), (0, 1, p1 - E), (0, 1, p3 - E)]
+
+
+def _brute_locations(read, db, k, w, can, E, min_seeds, top_n, max_occ):
+    """Mapping locations of one read from a brute-force seed enumeration (db from
+    _brute_db): matches of keys with more than max_occ occurrences skipped, then greedy
+    diagonal bands per (genome, strand), at least min_seeds matches, ranked by seeds
+    descending then genome, strand, first diagonal; (genome, strand, wstart, seeds)."""
+    n = len(read)
+    hits = []
+    for (rp, code, rst) in brute_minimizers(read, k, w, can):
+        occ = db.get(code, [])
+        if len(occ) > max_occ:
+            continue
+        for (g, gp, gst) in occ:
+            rel = rst ^ gst
+            hits.append((g, rel, gp - (n - k - rp if rel else rp)))
+    hits.sort()
+    locs, i = [], 0
+    while i < len(hits):
+        g, rel, d0 = hits[i]
+        j = i + 1
+        while j < len(hits) and hits[j][0] == g and hits[j][1] == rel and hits[j][2] <= d0 + E:
+            j += 1
+        if j - i >= min_seeds:
+            locs.append((-(j - i), g, rel, d0))
+        i = j
+    locs.sort()
+    return [(g, rel, d0 - E, -s) for (s, g, rel, d0) in locs[:top_n]]
+
+
+def test_mapping_repeat_filter_at_the_exact_occurrence_count(oracle_lib):
+    """The repeat filter at mapping time (Methods, "Index Construction & Querying": minimap2
+    skips over-represented minimizers; reading: a key with more than max_occ occurrences is
+    skipped). A 120-base segment X sits in genomes 0, 1 and 2, so its minimizers occur three
+    times; reads spanning X are mapped with max_occ = 3 (X's matches count: 3 is not more
+    than 3) and with max_occ = 2 (they are skipped). Expected locations come from a
+    brute-force enumeration of every genome's minimizers, with the filter applied here; the
+    two settings give different expected locations, so the boundary decides the test."""
+    rng = np.random.default_rng(43)
+    k, w, can, E = 11, 5, 1, 5
+    X = "".join(rng.choice(list("ACGT"), 120))
+    f = _rand_genomes(rng, [400, 500, 300, 450, 350, 600, 900])
+    gs = [f[0] + X + f[1], f[2] + X + f[3], f[4] + X[::-1].translate(_RC) + f[5], f[6]]
+    seq, off = _pack(gs)
+    ix = oracle.Index(seq, off, k, w, can)
+    db = _brute_db(gs, k, w, can)
+    x_codes = {code for (_, code, _) in brute_minimizers(X, k, w, can)}
+    assert x_codes and all(len(db[c]) == 3 for c in x_codes)
+    reads = []
+    for t in range(12):
+        a = int(rng.integers(len(f[0]) - 80, len(f[0]) + 40))
+        r = gs[0][a:a + 150]
+        reads.append(r[::-1].translate(_RC) if t % 2 else r)
+    reads.append(X)
+    rs, ro = _pack(reads)
+    expect = {}
+    for max_occ in (3, 2):
+        prm = oracle.params(e_abs=E, e_permille=0, min_seeds=2, top_n=3, max_occ=max_occ)
+        res = oracle.classify(ix, rs, ro, prm)
+        # a genome is dropped only with no counted match at all (tiny batch, cutoff 1e-4)
+        assert res["keep"].tolist()[:3] == ([1, 1, 1] if max_occ == 3 else [1, 0, 0])
+        expect[max_occ] = []
+        for i, r in enumerate(reads):
+            exp = _brute_locations(r, db, k, w, can, E, 2, 3, max_occ)
+            got = [(int(L["genome"]), int(L["strand"]), int(L["wstart"]), int(L["seeds"]))
+                   for L in res["locs"][i][:res["nloc"][i]]]
+            assert got == exp, (max_occ, i)
+            expect[max_occ].append(exp)
+    assert expect[3] != expect[2]
+    # the read X itself: three locations at max_occ = 3, none at max_occ = 2
+    assert len(expect[3][-1]) == 3 and expect[2][-1] == []
