@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import hashlib
 import math
 import os
 import subprocess
@@ -40,10 +41,18 @@ def _assemble_lib():
         if _LIB is None:
             src = os.path.join(_HERE, "_assemble.c")
             so = os.path.join(_HERE, "_assemble.so")
-            if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(src):
+            cmd = ["gcc", "-O2", "-shared", "-fPIC"]
+            with open(src, "rb") as f:
+                want = hashlib.sha256(repr(cmd).encode() + f.read()).hexdigest()
+            stamp = so + ".sha256"
+            have = open(stamp).read().strip() if os.path.exists(stamp) else ""
+            if not os.path.exists(so) or have != want:   # rebuilt on a content change, not on file times
                 tmp = so + ".%d.tmp" % os.getpid()
-                subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src])
+                subprocess.check_call(cmd + ["-o", tmp, src])
                 os.replace(tmp, so)
+                with open(stamp + ".tmp", "w") as f:
+                    f.write(want + "\n")
+                os.replace(stamp + ".tmp", stamp)
             _LIB = ctypes.CDLL(so)
             _LIB.gen_assemble.restype = ctypes.c_int
         return _LIB

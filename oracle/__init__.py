@@ -24,6 +24,7 @@ rank tie-breaks, repeat filter, window edges, multi-read split) has such a pin.
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
 import subprocess
 import threading
@@ -42,13 +43,24 @@ LOC_DTYPE = np.dtype({"names": ["wstart", "genome", "seeds", "strand", "dist"],
                       "offsets": [0, 8, 12, 16, 17], "itemsize": 24})
 
 
+_CMD = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread"]
+
+
 def build() -> str:
-    """Compile the oracle with gcc (plain C, -O2, no machine-specific flags)."""
+    """Compile the oracle with gcc (plain C, -O2, no machine-specific flags); rebuilt whenever
+    the SHA-256 of the command and the source differs from the one it was built from."""
     with _lock:
-        if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        with open(_SRC, "rb") as f:
+            want = hashlib.sha256(repr(_CMD).encode() + f.read()).hexdigest()
+        stamp = _SO + ".sha256"
+        have = open(stamp).read().strip() if os.path.exists(stamp) else ""
+        if not os.path.exists(_SO) or have != want:
             tmp = _SO + ".%d.tmp" % os.getpid()
-            subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
+            subprocess.check_call(_CMD + ["-o", tmp, _SRC])
             os.replace(tmp, _SO)
+            with open(stamp + ".tmp", "w") as f:
+                f.write(want + "\n")
+            os.replace(stamp + ".tmp", stamp)
     return _SO
 
 

@@ -5,6 +5,7 @@ CUDA runtime linked statically; nothing is installed outside the package directo
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -27,16 +28,33 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA library cannot be built")
 
 
-def _deps():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+STAMP = os.path.join(BUILD, "libmt.sha256")
+
+
+def source_hash() -> str:
+    """SHA-256 over the compiler command and the bytes of every source and header the library
+    is built from (csrc/ and include/mt.h), in a fixed order."""
+    h = hashlib.sha256()
+    h.update(repr((ARCH, FLAGS, SOURCES)).encode())
+    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC))
     files.append(os.path.join(HERE, "..", "include", "mt.h"))
-    return max(os.path.getmtime(f) for f in files if os.path.exists(f))
+    for f in files:
+        if os.path.isfile(f):
+            h.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every source under csrc/ for sm_103a and link libmt.so. Returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
-        return LIB
+    """Compile every source under csrc/ for sm_103a and link libmt.so. Returns its path. The
+    library is rebuilt whenever the sources' content hash differs from the one it was built
+    from (file times are not trusted: copies and checkouts change them)."""
+    want = source_hash()
+    if not force and os.path.exists(LIB) and os.path.exists(STAMP):
+        with open(STAMP) as f:
+            if f.read().strip() == want:
+                return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
@@ -59,6 +77,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as f:
+        f.write(want + "\n")
+    os.replace(STAMP + ".tmp", STAMP)
     return LIB
 
 
