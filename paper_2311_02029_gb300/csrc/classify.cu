@@ -30,7 +30,7 @@ int launch_classify_eda(const IndexView &ix, const uint64_t *rw, const IoBlock *
                         const uint32_t *cl, const uint64_t *cl_count, uint64_t max_items,
                         const Cluster *cand, uint32_t top_n, uint32_t e_abs, uint32_t e_permille,
                         uint32_t maxn, uint32_t maxE, uint32_t mode, uint8_t *dist,
-                        unsigned long long *counter, cudaStream_t s, bool allow_tune);
+                        unsigned long long *counter, cudaStream_t s, bool tune, mt_eda_shape *used);
 
 static constexpr unsigned FULL = 0xffffffffu;
 static constexpr int SEED_WARPS = 8;
@@ -38,6 +38,8 @@ static constexpr int SEED_THREADS = SEED_WARPS * 32;
 static constexpr uint32_t TILE = 128;                     // windows per tile
 static constexpr uint32_t KEYS = TILE + MT_MAX_W + 4;     // k-mers a tile may read (<= TILE+w+2)
 static constexpr uint32_t HCAP = 256;                     // seed matches held per read
+static constexpr uint32_t W11_TILE = 150;                 // windows per pass of the w = 11 path
+static constexpr uint32_t MPOS = W11_TILE > TILE ? W11_TILE : TILE;   // minimizers a pass may select
 static constexpr uint32_t RDW = MT_MAX_READ_LEN / 32 + 2;
 static constexpr uint32_t CSTORE = 8;                     // locations stored per read
 static constexpr uint32_t QOVF = 0xFFFFFFFFu;
@@ -56,7 +58,7 @@ struct WarpSmem {
         struct {
             uint64_t key[KEYS];     // k-mer keys of the tile
             uint64_t code[KEYS];    // canonical code | strand << 63
-            uint16_t mpos[TILE];    // minimizer positions of the tile
+            uint16_t mpos[MPOS];    // minimizer positions of the tile
             // lookups of one round, by rank among those with matches
             uint64_t e_w[32 * 3];   // inline occurrences, or the occurrence-list offset
             uint32_t e_pre[32];     // first match of the lookup within the round
@@ -276,8 +278,8 @@ template <> struct HitKey<false> {
     MT_DEV uint64_t wide(T h) const { return h; }
 };
 
-// Bitonic sort of 32*R keys held in registers: element r*32 + lane in v[r]. Exchanges across
-// lanes use shuffles, exchanges across register slots stay in the lane.
+// Bitonic sort of 32*R keys held in registers, ascending: element r*32 + lane in v[r].
+// Exchanges across lanes use shuffles, exchanges across register slots stay in the lane.
 template <int R, typename T>
 MT_DEV void bitonic_regs(T (&v)[R]) {
     const uint32_t lane = lane_id();
@@ -294,9 +296,8 @@ MT_DEV void bitonic_regs(T (&v)[R]) {
                         const uint32_t i = (uint32_t)r * 32u + lane;
                         const bool up = (i & k) == 0;
                         const T a = v[r], b = v[pr];
-                        const bool sw = (a > b) == up;
-                        v[r] = sw ? b : a;
-                        v[pr] = sw ? a : b;
+                        v[r] = up ? min(a, b) : max(a, b);
+                        v[pr] = up ? max(a, b) : min(a, b);
                     }
                 }
             } else {
@@ -304,9 +305,9 @@ MT_DEV void bitonic_regs(T (&v)[R]) {
                 for (int r = 0; r < R; r++) {
                     const uint32_t i = (uint32_t)r * 32u + lane;
                     const T o = __shfl_xor_sync(FULL, v[r], j);
-                    const bool up = (i & k) == 0;
-                    const bool lower = (lane & j) == 0;
-                    v[r] = (lower == up) ? (v[r] < o ? v[r] : o) : (v[r] < o ? o : v[r]);
+                    // keep the smaller key where this lane's bit j agrees with the block's direction
+                    const bool keep_min = ((i & k) == 0) == ((lane & j) == 0);
+                    v[r] = keep_min ? min(v[r], o) : max(v[r], o);
                 }
             }
         }
@@ -349,11 +350,12 @@ MT_DEV void warp_bitonic(T *a, uint32_t P) {
     }
 }
 
-// Up to 64 matches are sorted in registers; the rare larger sets (<= HCAP) in shared memory.
+// Up to 128 matches are sorted in registers; the rare larger sets (<= HCAP) in shared memory.
 template <typename T>
 MT_DEV void sort_hits(T *h, uint32_t H) {
     if (H <= 32) sort_regs<1, T>(h, H);
     else if (H <= 64) sort_regs<2, T>(h, H);
+    else if (H <= 128) sort_regs<4, T>(h, H);
     else {
         uint32_t P = 128;
         while (P < H) P <<= 1;
@@ -363,12 +365,129 @@ MT_DEV void sort_hits(T *h, uint32_t H) {
     }
 }
 
+// Top 32 bits of the k-mer key mix64(code) of a code below 2^56 (k <= 28), from the first
+// multiply, the middle xor-shift and the high word of the second multiply (the last xor-shift
+// changes only bit 0 of them). z >> 30 then fits in 32 bits, so the first xor-shift touches
+// the low word only.
+MT_DEV uint32_t mix64_hi(uint64_t z) {
+    z = (z ^ (uint64_t)(uint32_t)(z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z ^= z >> 27;
+    const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+    return __umulhi(lo, 0x133111ebu) + lo * 0x94d049bbu + hi * 0x133111ebu;
+}
+
+// (w,k)-minimizers of one pass over the windows [t0, t0 + tw) of a read for w = 11, k <= 28
+// (tw <= W11_TILE). Lane l computes the k-mers at local positions 5l .. 5l + 4 from one 32-base
+// slice of the packed read (forward codes from the slice's 2-bit reversal, reverse-complement
+// codes from its complement) and stores code | strand << 63 at code[local position]. A window
+// of 11 k-mers starting at local 5l + a (a < 5) is the last 5 - a k-mers of lane l, all five
+// of lane l + 1 and the first a + 1 of lane l + 2, so its minimum is min(suffix_l[a],
+// block_{l+1}, prefix_{l+2}[a]) (van Herk / Gil-Werman with blocks of five). Minima are taken
+// on 32-bit words (key bits 40..63) << 8 | local position, so one unsigned min orders by key
+// and keeps the leftmost of equal words. The same minima with the position bits reversed find
+// the rightmost k-mer of the smallest top bits; when the two differ, two k-mers of the window
+// share them and the window is redone on full 64-bit keys. Appends the selected positions
+// (absolute, each once) to mpos and returns their number; carry is the selection of the
+// previous pass's last window (-1 before the first pass).
+template <typename HitT>
+MT_DEV uint32_t minimizers_w11(WarpSmem<HitT> &ws, uint32_t t0, uint32_t tw, uint32_t k, uint32_t canonical,
+                               int32_t &carry) {
+    const uint32_t lane = lane_id();
+    const uint32_t b = 5u * lane;                 // first local position of this lane
+    uint32_t v[5], u[5];                          // leftmost / rightmost words
+    {
+        // every lane computes its five k-mers without branching; positions at or past tw + 10
+        // (past the pass's last k-mer) read zero or stale words (the slice's word index is
+        // clamped to the read buffer), but no window of the pass reaches them: window
+        // 5l + a < tw ends at 5l + a + 10 < tw + 10, and
+        // its three parts (suffix of lane l, lane l + 1, prefix of lane l + 2) hold only its
+        // own positions
+        const uint64_t mask = (1ull << (2 * k)) - 1;
+        const uint32_t p = min(t0 + b, 32u * (RDW - 2));
+        const uint64_t x = get32(ws.rd, p);                       // bases t0+b.., first lowest
+        const uint64_t nx = ~x;
+        const uint64_t rv = rev2(x) >> (56 - 2 * k);              // forward code of k-mer 4 in bits 0..2k-1
+#pragma unroll
+        for (int i = 0; i < 5; i++) {
+            const uint64_t rc = (nx >> (2 * i)) & mask;
+            const uint64_t fwd = (rv >> (8 - 2 * i)) & mask;
+            const bool r = canonical && rc < fwd;
+            const uint64_t code = r ? rc : fwd;
+            ws.u.t.code[b + i] = code | ((uint64_t)r << 63);
+            v[i] = (mix64_hi(code) & 0xFFFFFF00u) | (b + i);
+            u[i] = v[i] ^ 0xFFu;                                  // position bits reversed: 255 - (b + i)
+        }
+    }
+    uint32_t sel[5];
+    bool tie[5];
+    {
+        uint32_t pre[5], suf[5], qre[5], quf[5];
+        pre[0] = v[0]; qre[0] = u[0];
+#pragma unroll
+        for (int i = 1; i < 5; i++) { pre[i] = min(pre[i - 1], v[i]); qre[i] = min(qre[i - 1], u[i]); }
+        suf[4] = v[4]; quf[4] = u[4];
+#pragma unroll
+        for (int i = 3; i >= 0; i--) { suf[i] = min(v[i], suf[i + 1]); quf[i] = min(u[i], quf[i + 1]); }
+        const uint32_t f1 = __shfl_down_sync(FULL, pre[4], 1), g1 = __shfl_down_sync(FULL, qre[4], 1);
+#pragma unroll
+        for (int a = 0; a < 5; a++) {
+            const uint32_t p2 = __shfl_down_sync(FULL, pre[a], 2), q2 = __shfl_down_sync(FULL, qre[a], 2);
+            const uint32_t m = min(min(suf[a], f1), p2), q = min(min(quf[a], g1), q2);
+            sel[a] = t0 + (m & 0xFFu);
+            tie[a] = b + a < tw && ((m ^ q) & 0xFFu) != 0xFFu;
+        }
+    }
+    __syncwarp();                                 // codes of the pass are in shared memory
+    uint32_t tied = 0;
+#pragma unroll
+    for (int a = 0; a < 5; a++) tied |= (uint32_t)tie[a] << a;
+    if (__any_sync(FULL, tied != 0)) {
+        while (tied) {                            // leftmost smallest full key of the window
+            const uint32_t a = __ffs(tied) - 1;
+            tied &= tied - 1;
+            const uint32_t j = b + a;
+            uint32_t best = j;
+            uint64_t bk = mix64(ws.u.t.code[j] & CODE_MASK62);
+            for (uint32_t t = j + 1; t < j + 11; t++) {
+                const uint64_t kk = mix64(ws.u.t.code[t] & CODE_MASK62);
+                if (kk < bk) { bk = kk; best = t; }
+            }
+#pragma unroll
+            for (int q = 0; q < 5; q++) if ((uint32_t)q == a) sel[q] = t0 + best;
+        }
+    }
+    // each selected position once: a window's selection is new when it differs from the
+    // previous window's (selections never decrease along the read)
+    int32_t prv = __shfl_up_sync(FULL, (int32_t)sel[4], 1);
+    if (lane == 0) prv = carry;
+    bool em[5];
+    uint32_t ne = 0;
+#pragma unroll
+    for (int a = 0; a < 5; a++) {
+        const bool ok = b + a < tw;
+        em[a] = ok && (int32_t)sel[a] != prv;
+        ne += em[a];
+        if (ok) prv = (int32_t)sel[a];
+    }
+    const uint32_t incl = warp_incl_scan(ne);
+    uint32_t o = incl - ne;
+#pragma unroll
+    for (int a = 0; a < 5; a++)
+        if (em[a]) ws.u.t.mpos[o++] = (uint16_t)sel[a];
+    // prv is now the selection of the lane's last window: the pass's last window's, for the next
+    carry = __shfl_sync(FULL, prv, (tw - 1) / 5u);
+    return __shfl_sync(FULL, incl, 31);
+}
+
 // COUNT: containment only (every occurrence of every minimizer counted per genome, no
 // locations, no outputs per read); HPC: the reads' seeds are taken after homopolymer
 // compression (an index built with MT_INDEX_HPC).
-template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false>
+// W11: the index has w = 11 and k <= 28, and the minimizers come from the block path
+// (minimizers_w11); otherwise the general window-minimum path runs.
+template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false, bool W11 = false>
 __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
     static_assert(!MULTI || (COUNT && !HK32), "several indexes are only counted");
+    static_assert(!(MULTI && W11), "the block path keeps no keys for several tables");
     using HitT = typename HitKey<HK32>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
     unsigned long long *hist = reinterpret_cast<unsigned long long *>(smraw);
@@ -417,9 +536,15 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
         uint32_t H = 0;
         bool ovf = COUNT;   // counting only from the start
         int32_t carry = -1;
-        for (uint32_t t0 = 0; t0 < nwin; t0 += TILE) {
-            const uint32_t tw = min(TILE, nwin - t0);
+        constexpr bool w11 = W11;
+        const uint32_t tile = w11 ? W11_TILE : TILE;
+        for (uint32_t t0 = 0; t0 < nwin; t0 += tile) {
+            const uint32_t tw = min(tile, nwin - t0);
             const uint32_t npos = tw + w - 1;
+            uint32_t nm = 0;
+            if constexpr (W11) {
+                nm = minimizers_w11(ws, t0, tw, k, canonical, carry);
+            } else {
             // codes and keys of the tile's k-mers
             for (uint32_t i = lane; i < npos; i += 32) {
                 uint64_t fwd, rc, code;
@@ -433,7 +558,6 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             // (w,k)-minimizers: leftmost smallest key of each window, each position once.
             // Lane l takes windows 4l..4l+3 of the tile; for w >= 4 the four windows share
             // the k-mers [4l+3, 4l+w-1], so that minimum is found once.
-            uint32_t nm = 0;
             {
                 const uint64_t *key = ws.u.t.key;
                 const uint32_t j0 = 4 * lane;
@@ -504,6 +628,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
 #pragma unroll
                 for (int a = 1; a < 4; a++) if (((tw - 1) & 3) == (uint32_t)a) lastsel = sel[a];
                 carry = __shfl_sync(FULL, lastsel, last_lane);
+            }
             }
             __syncwarp();
             n_mins += nm;
@@ -608,7 +733,9 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                     rpos = ws.u.t.mpos[m];
                     const uint32_t xi = rpos - t0;
                     const uint64_t cs = ws.u.t.code[xi];
-                    const uint64_t key = ws.u.t.key[xi];
+                    uint64_t key;
+                    if constexpr (W11) key = mix64(cs & CODE_MASK62);
+                    else key = ws.u.t.key[xi];
                     rst = (uint32_t)(cs >> 63);
                     const uint64_t want = (cs & CODE_MASK62) + 1;
                     uint64_t s = slot_of(key, A.ix.slot_shift);
@@ -1390,7 +1517,7 @@ struct EnqueueCtx {
     unsigned char *ws;
     uint64_t cap_reads;
     uint32_t maxn, maxE;
-    bool allow_tune;
+    bool tune;             // time the approximation kernel's shapes on this batch (autotune calls)
     cudaEvent_t *ev;       // 5 events or null
     uint64_t launches;
     mt_allreduce_fn xfn;   // sum over the ranks of a sharded batch, or null
@@ -1403,6 +1530,7 @@ struct EnqueueCtx {
     const uint64_t *chunk_r;
     const cudaEvent_t *chunk_ev;
     bool capturing;           // the enqueue is being captured: chunk events are external waits
+    mt_eda_shape *shape = nullptr;   // receives the approximation kernel's shape, or null
 };
 
 // Replaces the G-vector at `dev` with its sum over the ranks of a sharded batch (a no-op for an
@@ -1418,9 +1546,13 @@ static int exchange(const EnqueueCtx &c, cudaStream_t s, void *dev, uint32_t G, 
     return MT_OK;
 }
 
-template <bool SH, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false>
+// The seeding kernel's block path serves indexes with w = 11 and k <= 28 (minimap2's short-read
+// seeds, the mapping index of the paper's read mapper).
+static bool seed_w11(const mt_index *ix) { return ix->w == 11 && ix->k <= 28; }
+
+template <bool SH, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false, bool W11 = false>
 static int launch_seed(const SeedArgs &A, size_t smem, uint64_t need, cudaStream_t s) {
-    auto kern = k_seed<SH, HK32, COUNT, HPC, MULTI>;
+    auto kern = k_seed<SH, HK32, COUNT, HPC, MULTI, W11>;
     MT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SEED_THREADS, smem));
@@ -1437,7 +1569,16 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
     const mt_index *ix = c.ix;
     const uint32_t G = ix->G, top_n = p->top_n;
     auto P = [&](size_t off) { return (void *)(c.ws + off); };
-    auto mark = [&](int i) { if (c.ev) cudaEventRecord(c.ev[i], s); };
+    static const char *const stage_name[5] = {
+        "mt stage 1-2c: pack, minimizers, lookups, containment counts, locations",
+        "mt stage 1d-2c: containment cutoff, candidate selection", "mt stage 2d: edit-distance approximation",
+        "mt stage 3: decision, multi-mapped split, abundances", nullptr};
+    StageTrace trace;
+    auto mark = [&](int i) {
+        if (c.ev) cudaEventRecord(c.ev[i], s);
+        if (stage_name[i]) trace.next(stage_name[i]);
+        else if (trace.open) { nvtxRangePop(); trace.open = false; }
+    };
     Counters *ctr = (Counters *)P(L.ctr);
     unsigned long long *ghits = (unsigned long long *)P(L.ghits);
     unsigned long long *U = (unsigned long long *)P(L.U);
@@ -1467,6 +1608,11 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
             A.r_begin = rb;
             A.r_end = re;
             const uint64_t need = (std::min<uint64_t>(re, c.cap_reads) - rb + SEED_WARPS - 1) / SEED_WARPS;
+            if (seed_w11(ix))
+                return hk32 ? (smem_hist ? launch_seed<true, true, false, false, false, true>(A, smem, need, s)
+                                         : launch_seed<false, true, false, false, false, true>(A, smem, need, s))
+                            : (smem_hist ? launch_seed<true, false, false, false, false, true>(A, smem, need, s)
+                                         : launch_seed<false, false, false, false, false, true>(A, smem, need, s));
             return hk32 ? (smem_hist ? launch_seed<true, true>(A, smem, need, s) : launch_seed<false, true>(A, smem, need, s))
                         : (smem_hist ? launch_seed<true, false>(A, smem, need, s) : launch_seed<false, false>(A, smem, need, s));
         };
@@ -1514,7 +1660,7 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
 
         rc = launch_classify_eda(iv, A.rw, io, (const uint32_t *)P(L.cl), &ctr->cl_count, c.cap_reads * top_n,
                                      (const Cluster *)P(L.cand), top_n, p->e_abs, p->e_permille, c.maxn, c.maxE,
-                                     p->eda_mode, (uint8_t *)P(L.dist), &ctr->eda_counter, s, c.allow_tune);
+                                     p->eda_mode, (uint8_t *)P(L.dist), &ctr->eda_counter, s, c.tune, c.shape);
         if (rc) return rc;
         mark(3);
 
@@ -1612,9 +1758,10 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
                          uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
                          mt_allreduce_fn xfn, void *xctx, const uint8_t *keep_in, int32_t *taxon,
                          uint8_t *nloc, mt_loc *locs, uint64_t *genome_hits, double *abundance,
-                         mt_stats *stats) {
+                         mt_stats *stats, bool tune = false, mt_eda_shape *shape = nullptr) {
     if (!ix || !offsets || (!taxon && n_reads) || (!reads && n_bases)) return MT_EINVAL;
     if (ix->hpc) return MT_EINVAL;   // a containment index: positions are in compressed coordinates
+    Trace trace("mt_classify");
     int rc = check_params(p);
     if (rc) return rc;
     if (n_reads >= 0xFFFFFFFFull / MT_MAX_TOPN) return MT_EINVAL;
@@ -1634,7 +1781,7 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
             MT_CK(cudaMemcpyAsync(d_roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
         }
         Counters *pre = nullptr;
-        if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) return rc;
+        if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) { if (d_roff) dfree(d_roff, s); return rc; }
         MT_CK(cudaMemsetAsync(pre, 0, sizeof(Counters), s));
         unsigned blocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 4);
         k_maxlen<<<blocks, 256, 0, s>>>(host_io ? d_roff : offsets, n_reads, n_bases, pre);
@@ -1726,13 +1873,14 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     if (stats)
         for (auto &e : ev) MT_CK(cudaEventCreate(&e));
-    EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, true, stats ? ev : nullptr, launches,
+    EnqueueCtx ctx{ix, p, &L, ws, n_reads, std::max<uint32_t>(maxn, 1), maxE, tune, stats ? ev : nullptr, launches,
                    xfn, xctx, keep_in, !host_io, 0, nullptr, nullptr};
     if (cs) {
         ctx.n_chunks = (uint32_t)(chunk_r.size() - 1);
         ctx.chunk_r = chunk_r.data();
         ctx.chunk_ev = chunk_ev.data() + 1;
     }
+    ctx.shape = shape;
     rc = enqueue_classify(ctx, s);
     if (rc) {
         if (cs) cudaStreamSynchronize(cs);
@@ -1769,6 +1917,19 @@ extern "C" int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_
                          taxon, nloc, locs, genome_hits, abundance, stats);
 }
 
+extern "C" int mt_classify_autotune(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
+                                    const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *p,
+                                    int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                                    uint64_t *genome_hits, double *abundance, mt_stats *stats,
+                                    mt_eda_shape *shape) {
+    if (shape) memset(shape, 0, sizeof(*shape));
+    const bool tune = p && (p->eda_mode & 15u) == MT_EDA_BATCHED;
+    int rc = classify_impl(ix, reads, n_bases, offsets, n_reads, p, device_ptrs, stream, nullptr, nullptr, nullptr,
+                           taxon, nloc, locs, genome_hits, abundance, stats, tune, shape);
+    if (shape && shape->lanes_per_pair) shape->tuned = tune ? 1u : 0u;
+    return rc;
+}
+
 extern "C" int mt_classify_masked(const mt_index *ix, const uint8_t *reads, uint64_t n_bases, const uint64_t *offsets,
                                   uint64_t n_reads, const mt_classify_params *p, int device_ptrs, void *stream,
                                   const uint8_t *keep, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
@@ -1794,6 +1955,7 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
                               int device_ptrs, void *stream, uint64_t *genome_hits, uint8_t *keep) {
     if (!ix || !offsets || (!reads && n_bases) || !genome_hits) return MT_EINVAL;
     if (max_occ > MT_MAX_OCC_LIMIT || cont_den == 0) return MT_EINVAL;
+    Trace trace("mt_containment");
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t G = ix->G;
     const bool host_io = !device_ptrs;
@@ -1852,6 +2014,8 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
         const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
         if (ix->hpc) rc = smem_hist ? launch_seed<true, false, true, true>(A, smem, need, s)
                                     : launch_seed<false, false, true, true>(A, smem, need, s);
+        else if (seed_w11(ix)) rc = smem_hist ? launch_seed<true, false, true, false, false, true>(A, smem, need, s)
+                                              : launch_seed<false, false, true, false, false, true>(A, smem, need, s);
         else rc = smem_hist ? launch_seed<true, false, true, false>(A, smem, need, s)
                             : launch_seed<false, false, true, false>(A, smem, need, s);
         if (rc) return fail(rc);
@@ -2026,6 +2190,7 @@ struct mt_plan {
     cudaEvent_t chunk_ev[MAX_CHUNKS] = {};
     cudaEvent_t ready = nullptr;
     cudaStream_t copy_stream = nullptr;
+    cudaEvent_t t_ev[2] = {};          // timing of a call's enqueue (stats), owned by the plan
 };
 
 extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, uint64_t max_reads,
@@ -2045,7 +2210,7 @@ extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, u
     pl->max_len = max_read_len;
     pl->maxE = maxE;
     pl->L = plan_layout(ix, max_bases, max_reads, p->top_n, max_read_len, p->max_occ, true);
-    cudaError_t e = cudaMalloc((void **)&pl->ws, pl->L.total);
+    cudaError_t e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc((void **)&pl->ws, pl->L.total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete pl;
@@ -2063,7 +2228,8 @@ extern "C" int mt_plan_create(const mt_index *ix, const mt_classify_params *p, u
     pl->n_chunks = (uint32_t)std::min<uint64_t>(mt_plan::MAX_CHUNKS, std::max<uint64_t>(1, max_reads >> 17));
     for (uint32_t i = 0; i <= pl->n_chunks; i++) pl->chunk_r[i] = max_reads * i / pl->n_chunks;
     bool ok = cudaStreamCreateWithFlags(&pl->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&pl->ready, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&pl->ready, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreate(&pl->t_ev[0]) == cudaSuccess && cudaEventCreate(&pl->t_ev[1]) == cudaSuccess;
     for (uint32_t i = 0; ok && i < pl->n_chunks; i++)
         ok = cudaEventCreateWithFlags(&pl->chunk_ev[i], cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -2082,6 +2248,7 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
                                 mt_loc *locs, uint64_t *genome_hits, double *abundance, mt_stats *stats) {
     if (!pl || !offsets || (!taxon && n_reads) || (!reads && n_bases)) return MT_EINVAL;
     if (n_reads > pl->cap_reads || n_bases > pl->cap_bases) return MT_EINVAL;
+    Trace trace("mt_plan_classify");
     cudaStream_t s = (cudaStream_t)stream;
     const Layout &L = pl->L;
     const uint32_t G = pl->ix->G, top_n = pl->p.top_n;
@@ -2137,26 +2304,21 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
         for (uint32_t i = 0; i < pl->n_chunks; i++) MT_CK(cudaEventRecord(pl->chunk_ev[i], s));
     }
 
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    if (stats) {
-        MT_CK(cudaEventCreate(&ev[0]));
-        MT_CK(cudaEventCreate(&ev[1]));
-        MT_CK(cudaEventRecord(ev[0], s));
-    }
-    EnqueueCtx ctx{pl->ix, &pl->p, &L, pl->ws, pl->cap_reads, pl->max_len, pl->maxE, true, nullptr, 0};
+    cudaEvent_t *ev = pl->t_ev;
+    if (stats) MT_CK(cudaEventRecord(ev[0], s));
+    EnqueueCtx ctx{pl->ix, &pl->p, &L, pl->ws, pl->cap_reads, pl->max_len, pl->maxE, false, nullptr, 0};
     ctx.n_chunks = pl->n_chunks;
     ctx.chunk_r = pl->chunk_r;
     ctx.chunk_ev = pl->chunk_ev;
     int rc = MT_OK;
     if (pl->calls == 0) {
-        // the first call runs directly (it may autotune the approximation kernel)
+        // the first call runs directly
         rc = enqueue_classify(ctx, s);
         pl->launches = ctx.launches;
     } else {
         if (!pl->exec) {
             // capture on the plan's own stream (the caller's may be the legacy default
             // stream, which cannot be captured); the graph is then launched on the caller's
-            ctx.allow_tune = false;
             ctx.capturing = true;
             if (!pl->cap_stream) MT_CK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
             MT_CK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -2189,8 +2351,6 @@ extern "C" int mt_plan_classify(mt_plan *pl, const uint8_t *reads, uint64_t n_ba
         float ms = 0;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
         stats->ms_total = ms;
-        cudaEventDestroy(ev[0]);
-        cudaEventDestroy(ev[1]);
     }
     return status_of(h.err);
 }
@@ -2207,6 +2367,8 @@ extern "C" void mt_plan_destroy(mt_plan *pl) {
     for (uint32_t i = 0; i < mt_plan::MAX_CHUNKS; i++)
         if (pl->chunk_ev[i]) cudaEventDestroy(pl->chunk_ev[i]);
     if (pl->ready) cudaEventDestroy(pl->ready);
+    for (cudaEvent_t e : pl->t_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(pl->ws);
     cudaFreeHost(pl->h_io);
     cudaFreeHost(pl->h_ctr);

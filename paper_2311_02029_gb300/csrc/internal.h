@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -10,6 +11,26 @@
 #include "common.cuh"
 
 namespace mt {
+
+// NVTX ranges (host-side, shown by Nsight Systems and ncu's range filters; no cost without a
+// tool attached): Trace covers one scope, StageTrace a sequence of stages in one scope.
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
+struct StageTrace {
+    bool open = false;
+    void next(const char *name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~StageTrace() {
+        if (open) nvtxRangePop();
+    }
+};
 
 void set_cuda_error(cudaError_t e, const char *what);
 bool cuda_ok(cudaError_t e, const char *what);
@@ -25,6 +46,9 @@ const char *last_cuda_error();
 
 // Stream-ordered device allocation from the default memory pool (kept cached).
 int dalloc(void **p, size_t bytes, cudaStream_t s);
+// True when an injected allocation failure (mt_inject_alloc_failure) is due now; every
+// allocation of the library's calls asks once.
+bool alloc_fault();
 void dfree(void *p, cudaStream_t s);
 
 // Carves aligned sub-buffers out of one allocation.

@@ -97,9 +97,9 @@ def clade(mt):
     return c, g, r, ix, oix
 
 
-def test_clade_workload_warp_path_only(mt):
-    """The clade workload with w = 9: no thread-per-read kernel for it, every read is seeded by
-    the warp-per-read kernel."""
+def test_clade_workload_general_window_path(mt):
+    """The clade workload with w = 9: the seeding kernel's general window-minimum path (four
+    windows a lane over keys in shared memory) instead of the block path it takes for w = 11."""
     c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=5_000, w=9)
     g = gen.make_genomes(c)
     r = gen.make_reads(c, g)
@@ -136,8 +136,9 @@ def test_clade_parameter_sweep(mt, clade, kw):
 @pytest.mark.parametrize("kw", [(15, 10), (13, 7), (21, 11)])
 def test_mixed_lengths_and_edges(mt, kw):
     """Reads of 1..1024 bases (below k+w-1, exactly MT_MAX_READ_LEN), reads overhanging genome
-    ends on both strands, E from a per-mille threshold. w = 10 and 11 take the thread-per-read
-    seeding path (long reads handed to the warp kernel); w = 7 runs the warp kernel only."""
+    ends on both strands, E from a per-mille threshold. w = 10 and 7 run the general
+    window-minimum path; w = 11 the block path, whose passes cover 150 windows each, so reads
+    above 160 bases carry the last window's selection from pass to pass."""
     k, w = kw
     rng = np.random.default_rng(5)
     gs = [gen.ascii_of(rng.integers(0, 4, L, dtype=np.uint8)) for L in (3000, 1500, 5000)]
