@@ -83,7 +83,7 @@ typedef struct {
 
 /* Edit-distance approximation of each candidate, eda_mode = form | approximation.
  * Execution forms (identical results):                                                    */
-#define MT_EDA_BATCHED 0u  /* persistent work-stealing kernel, autotuned group shape */
+#define MT_EDA_BATCHED 0u  /* persistent work-stealing kernel, tuned (or default) group shape */
 #define MT_EDA_PLAIN 1u    /* one warp per pair, one launch per length bucket */
 /* Approximations (Table 1; the Discussion's O(n) count comparisons and O(nE) pigeonhole
  * filters). Each result is min(estimate, E + 1); a location is accepted iff it is <= E.
@@ -147,6 +147,16 @@ const char *mt_strerror(int status);
 const char *mt_last_cuda_error(void);
 int mt_version(void);
 
+/* ---- host-side fault injection and accounting, for tests (no counterpart in the paper) ----
+ * mt_inject_alloc_failure(n): the next n device allocations of the library's calls succeed and
+ * the one after fails as if the device were out of memory (the call returns MT_ENOMEM after
+ * freeing what it took); n < 0 turns injection off (the default). Every later allocation
+ * succeeds again once the injected failure has happened. Process-wide; it makes no GPU fault.
+ * mt_pool_used_bytes(): bytes currently allocated from the current device's stream-ordered
+ * pool by the library's calls and not yet freed (a call that returned holds none of them). */
+void mt_inject_alloc_failure(int64_t n);
+uint64_t mt_pool_used_bytes(void);
+
 /* ---- index (Methods, "Reference Database Organisation and Index Construction &
  * Querying"): every genome's (w,k)-minimizers, key = SplitMix64 finaliser of the k-mer
  * code, held in HBM as an open-addressing table of 32-byte slots (one DRAM sector per
@@ -208,6 +218,38 @@ int mt_classify(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
                 const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
                 int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
                 uint64_t *genome_hits, double *abundance, mt_stats *stats);
+
+/* Shape of the batched approximation kernel (MT_EDA_BATCHED) for one edit-threshold class
+ * (classes: E in [0,1], [2,3], [4,7], [8,15], [16,31], [32,63], [64,127]). No counterpart in
+ * the paper: the batching side of this library. */
+#define MT_EDA_CLASSES 8u
+typedef struct {
+    uint32_t lanes_per_pair;    /* lanes of a warp working on one pair: 1, 2, 4, 8, 16 or 32 */
+    uint32_t pairs_per_chunk;   /* pairs a warp takes from the shared counter at a time */
+    uint32_t cta_threads;       /* threads per CTA of the persistent launch (128 .. 1024) */
+    uint32_t refill;            /* SneakySnake, one lane per pair: 1 = a lane takes a new pair as
+                                   soon as its own ends; 0 = the warp's lanes take pairs together */
+    uint32_t tuned;             /* 1: chosen by an autotune call in this process; 0: the default */
+} mt_eda_shape;
+
+/* mt_classify that first times the batched approximation kernel's shapes on this batch's own
+ * candidates (lanes per pair in {1,2,4,8,16,32}; with one lane per pair, lanes refilled one by
+ * one or not; then pairs per chunk in {32,64,128,256}, then CTA size in {128,256,512,1024}; a
+ * few dozen launches on at most 2^17 candidates) and keeps the
+ * fastest for the batch's edit-threshold class on this device; the batch is then classified
+ * with it (outputs and errors exactly as mt_classify). mt_classify, plans and the serving loop
+ * never time anything themselves: they use the shape kept here, else the default. *shape
+ * (nullable) receives the shape used. Only eda_mode's batched form is tuned. */
+int mt_classify_autotune(const mt_index *ix, const uint8_t *reads, uint64_t n_bases,
+                         const uint64_t *offsets, uint64_t n_reads, const mt_classify_params *params,
+                         int device_ptrs, void *stream, int32_t *taxon, uint8_t *nloc, mt_loc *locs,
+                         uint64_t *genome_hits, double *abundance, mt_stats *stats, mt_eda_shape *shape);
+
+/* The shape the batched approximation kernel uses on this device for approximation `mode`
+ * (form bits ignored), pairs of edit threshold E, in classification (classification = 1) or in
+ * mt_eda_batch (0): the tuned one if an autotune call chose it, else the default.
+ * Errors: MT_EINVAL, MT_ECUDA. */
+int mt_eda_shape_for(uint32_t mode, int classification, uint32_t E, mt_eda_shape *out);
 
 /* ---- containment alone (Fig. 1 stage 1; "The MetaTrinity Pipeline") ------------------------
  * Seed hits per genome over the batch, counted with multiplicity for every minimizer of every
@@ -378,6 +420,15 @@ int mt_classify_genome_sharded(const mt_index *shard, const uint32_t *genome_ids
  * call uses no GPU. Errors: MT_EINVAL (a node index out of range, parent links with a cycle). */
 int mt_profile_rollup(const double *abundance, uint32_t n_genomes, const uint32_t *genome_node,
                       const int32_t *parent, uint32_t n_nodes, double *node_abundance);
+/* mt_profile_rollup on the device: abundance[n_genomes], genome_node[n_genomes], parent[n_nodes]
+ * and node_abundance[n_nodes] are DEVICE pointers (e.g. the abundance vector of a device-buffer
+ * mt_classify, which then needs no host pass); enqueued on `stream`, returns after
+ * synchronising it. Each genome's abundance is added to the taxa on its path in parallel, so
+ * the sums agree with mt_profile_rollup's up to the order of additions (within 1e-12 of 1).
+ * Errors: MT_EINVAL (a node index out of range, parent links with a cycle; node_abundance is
+ * then undefined), MT_ENOMEM, MT_ECUDA. */
+int mt_profile_rollup_device(const double *abundance, uint32_t n_genomes, const uint32_t *genome_node,
+                             const int32_t *parent, uint32_t n_nodes, double *node_abundance, void *stream);
 
 /* ---- batched form with a captured CUDA graph ---------------------------------------------
  * A plan holds a preallocated workspace sized for batches of up to max_reads reads,
@@ -419,13 +470,24 @@ int mt_pack_seqs(const uint8_t *seq, const uint64_t *offsets, uint64_t n_seqs, u
  * MT_MAX_E, read length <= MT_MAX_READ_LEN. dist[p] = the approximation of mode's
  * MT_EDA_* bits, min(estimate, E[p] + 1) (SneakySnake: obstacles; window bases all count as
  * genome bases here). All pointers are DEVICE pointers. mode = form | approximation, form
- * MT_EDA_BATCHED (one persistent work-stealing launch, autotuned lanes per pair) or
- * MT_EDA_PLAIN (one launch per read-length bucket, a warp per pair); both forms give
- * identical dist. The call returns after synchronising
- * `stream`. Errors: MT_EINVAL (length mismatch, limits), MT_ENOMEM, MT_ECUDA. */
+ * MT_EDA_BATCHED (one persistent work-stealing launch over the pairs ordered by E, each
+ * edit-threshold class with its tuned or default shape) or MT_EDA_PLAIN (one launch per
+ * read-length bucket, a warp per pair); both forms give identical dist. The call returns
+ * after synchronising `stream`. Errors: MT_EINVAL (length mismatch, limits), MT_ENOMEM,
+ * MT_ECUDA. */
 int mt_eda_batch(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
                  const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
                  const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist);
+
+/* mt_eda_batch that, in the batched form, first times the shapes (as mt_classify_autotune) on
+ * up to 2^17 pairs of every edit-threshold class in the batch, keeps the fastest per class on
+ * this device for later mt_eda_batch calls, and then computes dist with them. shapes (nullable,
+ * MT_EDA_CLASSES entries) receives each class's shape (zeros for classes not in the batch).
+ * The plain form is computed as by mt_eda_batch, nothing timed. Errors: as mt_eda_batch. */
+int mt_eda_batch_autotune(const uint64_t *read_words, const uint64_t *read_off, uint64_t n_reads,
+                          const uint64_t *win_words, const uint64_t *win_off, const uint32_t *pair_read,
+                          const uint16_t *E, uint64_t n_pairs, uint32_t mode, void *stream, uint8_t *dist,
+                          mt_eda_shape *shapes);
 
 /* ---- the same stage without any device allocation ----------------------------------------
  * No counterpart in the paper: an addition for callers that cannot allocate device memory
@@ -458,8 +520,12 @@ int mt_server_submit(mt_server *s, const uint8_t *reads, uint64_t n_bases, const
                      uint64_t *genome_hits, double *abundance, uint64_t *req_id);
 /* Waits up to timeout_ms (0 = just check) for a request. Returns MT_OK when done (its
  * outputs are written), MT_EBUSY / MT_ETIMEDOUT while pending, or the request's error.
- * If latency_s != NULL it receives submit-to-completion seconds. */
+ * If latency_s != NULL it receives submit-to-completion seconds. The poll that reports a
+ * final status (anything but MT_EBUSY / MT_ETIMEDOUT) releases the request: the server keeps
+ * nothing of it afterwards, and its id is unknown to later polls and cancels (MT_EINVAL). */
 int mt_server_poll(mt_server *s, uint64_t req_id, int timeout_ms, double *latency_s);
+/* Cancels a request still in the queue: MT_OK (a later poll reports MT_ECANCELED), MT_EBUSY
+ * when it is running or done but not yet polled, MT_EINVAL for an unknown or released id. */
 int mt_server_cancel(mt_server *s, uint64_t req_id);
 void mt_server_destroy(mt_server *s);
 

@@ -75,6 +75,18 @@ class Stats(ctypes.Structure):
                 for n, _ in self._fields_}
 
 
+class EdaShape(ctypes.Structure):
+    """``mt_eda_shape``: the batched approximation kernel's shape for one edit-threshold class."""
+    _fields_ = [("lanes_per_pair", ctypes.c_uint32), ("pairs_per_chunk", ctypes.c_uint32),
+                ("cta_threads", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("tuned", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+EDA_CLASSES = 8
+
+
 class IndexInfo(ctypes.Structure):
     _fields_ = [("n_genomes", ctypes.c_uint32), ("k", ctypes.c_uint32), ("w", ctypes.c_uint32),
                 ("canonical", ctypes.c_uint32), ("total_bases", ctypes.c_uint64),
@@ -89,7 +101,9 @@ EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", 
            "mt_eda_batch", "mt_eda_batch_noalloc", "mt_plan_create", "mt_plan_classify",
            "mt_plan_device_bytes", "mt_plan_destroy", "mt_server_create", "mt_server_submit", "mt_server_poll",
            "mt_server_cancel", "mt_server_destroy", "mt_part_create", "mt_part_contain", "mt_part_contain_batches", "mt_part_subset",
-           "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned", "mt_classify_genome_sharded"]
+           "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned", "mt_classify_genome_sharded",
+           "mt_inject_alloc_failure", "mt_pool_used_bytes", "mt_classify_autotune", "mt_eda_batch_autotune",
+           "mt_eda_shape_for", "mt_profile_rollup_device"]
 
 
 def lib():
@@ -105,6 +119,10 @@ def lib():
         L.mt_strerror.argtypes = [i32]
         L.mt_last_cuda_error.restype = ctypes.c_char_p
         L.mt_version.restype = i32
+        L.mt_inject_alloc_failure.restype = None
+        L.mt_inject_alloc_failure.argtypes = [ctypes.c_int64]
+        L.mt_pool_used_bytes.restype = u64
+        L.mt_pool_used_bytes.argtypes = []
         L.mt_build_index.restype = i32
         L.mt_build_index.argtypes = [vp, vp, u32, ctypes.POINTER(IndexParams), vp, ctypes.POINTER(vp)]
         L.mt_build_index_subset.restype = i32
@@ -112,6 +130,8 @@ def lib():
         L.mt_free_index.argtypes = [vp]
         L.mt_profile_rollup.restype = i32
         L.mt_profile_rollup.argtypes = [vp, u32, vp, vp, u32, vp]
+        L.mt_profile_rollup_device.restype = i32
+        L.mt_profile_rollup_device.argtypes = [vp, u32, vp, vp, u32, vp, vp]
         L.mt_save_index.restype = i32
         L.mt_save_index.argtypes = [vp, ctypes.c_char_p, vp]
         L.mt_load_index.restype = i32
@@ -123,6 +143,13 @@ def lib():
                                   vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
         L.mt_containment.restype = i32
         L.mt_containment.argtypes = [vp, vp, u64, vp, u64, u32, u32, u32, i32, vp, vp, vp]
+        L.mt_classify_autotune.restype = i32
+        L.mt_classify_autotune.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
+                                           vp, vp, vp, vp, vp, ctypes.POINTER(Stats), ctypes.POINTER(EdaShape)]
+        L.mt_eda_batch_autotune.restype = i32
+        L.mt_eda_batch_autotune.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp, vp]
+        L.mt_eda_shape_for.restype = i32
+        L.mt_eda_shape_for.argtypes = [u32, i32, u32, ctypes.POINTER(EdaShape)]
         L.mt_classify_masked.restype = i32
         L.mt_classify_masked.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
                                          vp, vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
@@ -301,15 +328,21 @@ def classify_params(e_abs=0, e_permille=100, min_seeds=3, top_n=3, max_occ=1024,
                           abund_cutoff)
 
 
-def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params, keep=None) -> dict:
-    """Marshalling shared by ``classify``, ``classify_sharded`` (cb: an AllreduceFn) and
-    ``classify_masked`` (keep: the genome mask)."""
+def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params, keep=None, tune=False) -> dict:
+    """Marshalling shared by ``classify``, ``classify_sharded`` (cb: an AllreduceFn),
+    ``classify_masked`` (keep: the genome mask) and ``classify_autotune`` (tune)."""
     p = classify_params(**params)
     st = Stats()
+    shape = EdaShape()
     G = ix.n_genomes
 
     def call(rptr, nb, optr, n_reads, dev):
         L = lib()
+        if tune:
+            return L.mt_classify_autotune(ix.handle, rptr, nb, optr, n_reads, ctypes.byref(p), dev, _stream(stream),
+                                          _ptr(out["taxon"]), _ptr(out["nloc"]), _ptr(out["locs"]),
+                                          _ptr(out["genome_hits"]), _ptr(out["abundance"]), ctypes.byref(st),
+                                          ctypes.byref(shape))
         if keep is not None:
             k = keep if dev else np.ascontiguousarray(_as_host(keep), dtype=np.uint8)
             return L.mt_classify_masked(ix.handle, rptr, nb, optr, n_reads, ctypes.byref(p), dev, _stream(stream),
@@ -344,8 +377,11 @@ def _classify(ix: Index, reads, offsets, cb, stream, want_locs, out, params, kee
         else:
             out = dict(out)
         rc = call(_ptr(r), len(r), _ptr(off), n_reads, 0)
-    _check(rc, "mt_classify_masked" if keep is not None else ("mt_classify" if cb is None else "mt_classify_sharded"))
+    _check(rc, "mt_classify_autotune" if tune else
+           ("mt_classify_masked" if keep is not None else ("mt_classify" if cb is None else "mt_classify_sharded")))
     out["stats"] = st.as_dict()
+    if tune:
+        out["eda_shape"] = shape.as_dict()
     return out
 
 
@@ -354,6 +390,21 @@ def classify(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None
     (results come back as numpy arrays) or CUDA tensors (results are CUDA tensors).
     ``out`` may hold preallocated host output arrays (e.g. in pinned memory)."""
     return _classify(ix, reads, offsets, None, stream, want_locs, out, params)
+
+
+def classify_autotune(ix: Index, reads, offsets, *, stream=None, want_locs=True, out=None, **params) -> dict:
+    """``mt_classify_autotune``: ``classify`` that first times the batched approximation kernel's
+    shapes on this batch's candidates and keeps the fastest for later calls on this device; the
+    result also holds ``eda_shape`` (the shape used)."""
+    return _classify(ix, reads, offsets, None, stream, want_locs, out, params, tune=True)
+
+
+def eda_shape_for(mode: int, classification: bool, E: int) -> dict:
+    """``mt_eda_shape_for``: the batched approximation kernel's shape (tuned or default) for
+    approximation ``mode`` and edit threshold E, in classification or in the EDA batch call."""
+    sh = EdaShape()
+    _check(lib().mt_eda_shape_for(mode, 1 if classification else 0, E, ctypes.byref(sh)), "mt_eda_shape_for")
+    return sh.as_dict()
 
 
 def classify_masked(ix: Index, reads, offsets, keep, *, stream=None, want_locs=True, out=None, **params) -> dict:
@@ -751,6 +802,20 @@ def eda_batch(read_words, read_off, win_words, win_off, pair_read, E, mode=MT_ED
     return dist
 
 
+def eda_batch_autotune(read_words, read_off, win_words, win_off, pair_read, E, mode=MT_EDA_BATCHED, stream=None):
+    """``mt_eda_batch_autotune``: ``eda_batch`` that first times the batched kernel's shapes on
+    every edit-threshold class of this batch and keeps the fastest per class; returns
+    (distances, list of the classes' shapes)."""
+    import torch
+    n_pairs = pair_read.numel()
+    dist = torch.empty(n_pairs, dtype=torch.uint8, device=pair_read.device)
+    shapes = (EdaShape * EDA_CLASSES)()
+    _check(lib().mt_eda_batch_autotune(_ptr(read_words), _ptr(read_off), read_off.numel() - 1, _ptr(win_words),
+                                       _ptr(win_off), _ptr(pair_read), _ptr(E), n_pairs, mode, _stream(stream),
+                                       _ptr(dist), ctypes.cast(shapes, ctypes.c_void_p)), "mt_eda_batch_autotune")
+    return dist, [sh.as_dict() for sh in shapes]
+
+
 NOALLOC_MAX_PAIRS = 1 << 20
 
 
@@ -816,6 +881,8 @@ class Server:
         rc = lib().mt_server_poll(self._h, req_id, timeout_ms, ctypes.byref(lat))
         if rc in (MT_EBUSY, MT_ETIMEDOUT):
             return rc, None, None
+        if req_id not in self._keep:          # unknown, or released by an earlier final poll
+            return rc, None, None
         _, _, out = self._keep.pop(req_id)
         return rc, lat.value, out
 
@@ -837,6 +904,16 @@ class Server:
 # ---- taxonomic profile (Fig. 1, 3b) ------------------------------------------------------------
 def _as_host(x):
     return x.cpu().numpy() if _is_torch(x) else np.asarray(x)
+
+
+def profile_rollup_device(abundance, genome_node, parent, stream=None):
+    """``mt_profile_rollup_device``: per-taxon abundance on the device (CUDA tensors: float64
+    abundance, int32 or uint32 genome nodes, int32 parents); returns a CUDA float64 tensor."""
+    import torch
+    out = torch.empty(parent.numel(), dtype=torch.float64, device=abundance.device)
+    _check(lib().mt_profile_rollup_device(_ptr(abundance), abundance.numel(), _ptr(genome_node), _ptr(parent),
+                                          parent.numel(), _ptr(out), _stream(stream)), "mt_profile_rollup_device")
+    return out
 
 
 def profile_rollup(abundance, genome_node, parent) -> np.ndarray:

@@ -6,6 +6,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -41,19 +42,40 @@ int sm_count() {
     return cached;
 }
 
-static std::once_flag g_pool_once;
+// Allocations left before an injected failure (-1: none injected).
+static std::atomic<int64_t> g_fail_after{-1};
+
+bool alloc_fault() {
+    int64_t v = g_fail_after.load();
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
+// The default pool of each device keeps freed blocks cached in this process; set once per
+// device, the first time the library allocates there.
+static std::mutex g_pool_mu;
+static uint64_t g_pool_set[4] = {0, 0, 0, 0};   // bit d: device d's pool configured
+
+static void configure_pool(int dev) {
+    if (dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (g_pool_set[dev >> 6] >> (dev & 63) & 1u) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_set[dev >> 6] |= 1ull << (dev & 63);
+}
 
 int dalloc(void **p, size_t bytes, cudaStream_t s) {
-    std::call_once(g_pool_once, [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            uint64_t thr = UINT64_MAX;   // keep freed blocks cached in this process
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
-        }
-    });
+    int dev = 0;
+    cudaGetDevice(&dev);
+    configure_pool(dev);
     *p = nullptr;
+    if (alloc_fault()) return MT_ENOMEM;
     if (bytes == 0) bytes = 256;
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e == cudaErrorMemoryAllocation) {
@@ -67,6 +89,21 @@ int dalloc(void **p, size_t bytes, cudaStream_t s) {
 void dfree(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
+
+}  // namespace mt
+
+extern "C" void mt_inject_alloc_failure(int64_t n) { mt::g_fail_after.store(n < 0 ? -1 : n); }
+
+extern "C" uint64_t mt_pool_used_bytes(void) {
+    int dev = 0;
+    cudaMemPool_t pool;
+    uint64_t used = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    return used;
+}
+
+namespace mt {
 
 // ---- 2-bit packing -----------------------------------------------------------------------
 // One thread per output word: the sequence owning the word is found by binary search over
@@ -595,6 +632,7 @@ static int build_checked(const uint8_t *genomes, const uint64_t *offsets, const 
 
 extern "C" int mt_build_index(const uint8_t *genomes, const uint64_t *offsets, uint32_t n_genomes,
                               const mt_index_params *p, void *stream, mt_index **out) {
+    Trace trace("mt_build_index");
     return build_checked(genomes, offsets, nullptr, n_genomes, p, stream, out);
 }
 

@@ -220,6 +220,7 @@ extern "C" int mt_server_poll(mt_server *s, uint64_t req_id, int timeout_ms, dou
         s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; });
     if (!r->done) return timeout_ms > 0 ? MT_ETIMEDOUT : MT_EBUSY;
     if (latency_s) latency_s[0] = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+    s->all.erase(req_id);   // reported: released (a long-running loop keeps no finished requests)
     return r->status;
 }
 
