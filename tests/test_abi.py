@@ -44,6 +44,7 @@ def test_struct_layouts_match_header(mtlib):
     assert mtlib.LOC_DTYPE.itemsize == 24
     assert ctypes.sizeof(mtlib.Stats) == 136
     assert ctypes.sizeof(mtlib.IndexInfo) == 64
+    assert ctypes.sizeof(mtlib.EdaShape) == 20
 
 
 def test_status_strings_and_argument_checks_without_gpu(mtlib):
@@ -209,3 +210,10 @@ def test_every_entry_point_refuses_null_arguments_without_gpu(mtlib):
     assert L.mt_server_submit(None, p, 8, p, 1, p, p, p, p, p, ctypes.byref(rid)) == E
     assert L.mt_server_poll(None, 1, 0, ctypes.byref(d)) == E
     assert L.mt_profile_rollup(None, 2, None, None, 0, None) == E
+    assert L.mt_profile_rollup_device(None, 2, None, None, 0, None, None) == E
+    sh = mtlib.EdaShape()
+    assert L.mt_eda_shape_for(0x70, 0, 8, ctypes.byref(sh)) == E                     # no such approximation
+    assert L.mt_eda_shape_for(0, 0, 200, ctypes.byref(sh)) == E                      # E above MT_MAX_E
+    assert L.mt_eda_batch_autotune(p, p, 1, p, p, p, p, 1, 99, None, p, None) == E   # no such form
+    assert L.mt_classify_autotune(None, p, 8, p, 1, ctypes.byref(cp), 0, None, p, p, p, p, p, ctypes.byref(st),
+                                  ctypes.byref(sh)) == E

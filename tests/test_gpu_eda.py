@@ -129,3 +129,56 @@ def test_eda_batch_rejects_bad_pairs(mt):
     d = mt.eda_batch(rw, ro, ww, wo, pr, E)   # still usable
     assert d.numel() == 1000
     torch.cuda.synchronize()
+
+
+def test_autotune_reports_keeps_and_does_not_change_results(mt):
+    """mt_eda_batch_autotune times the batched kernel's shapes per edit-threshold class and keeps
+    the fastest: the shapes it reports are valid, mt_eda_shape_for returns them afterwards, and
+    the distances (tuned call, later untuned batched call, plain call) equal the oracle's, also
+    with the extreme shapes (E = 0 and E = 127 in one call)."""
+    pairs = gen.make_eda_pairs(gen.config(3), n_pairs=300_000, seed=91)
+    dev = to_dev(pairs, mt)
+    ref = oracle.eda_batch(pairs, threads=8)
+    dist, shapes = mt.eda_batch_autotune(*dev)
+    assert np.array_equal(dist.cpu().numpy(), ref)
+    present = sorted({int(e).bit_length() - 1 if e >= 2 else 0 for e in np.unique(pairs.E)})
+    for c in range(mt.EDA_CLASSES):
+        sh = shapes[c]
+        if c in present:
+            assert sh["lanes_per_pair"] in (1, 2, 4, 8, 16, 32) and sh["tuned"] == 1
+            assert sh["pairs_per_chunk"] in (32, 64, 128, 256) and sh["cta_threads"] in (128, 256, 512, 1024)
+            assert sh["refill"] in (0, 1) and (sh["refill"] == 0 or sh["lanes_per_pair"] == 1)
+        else:
+            assert sh == {"lanes_per_pair": 0, "pairs_per_chunk": 0, "cta_threads": 0, "refill": 0, "tuned": 0}
+    for e in np.unique(pairs.E):
+        c = int(e).bit_length() - 1 if e >= 2 else 0
+        got = mt.eda_shape_for(0, False, int(e))
+        assert got == shapes[c]
+    for mode in (mt.MT_EDA_BATCHED, mt.MT_EDA_PLAIN):
+        assert np.array_equal(mt.eda_batch(*dev, mode=mode).cpu().numpy(), ref)
+
+
+def test_classify_tunes_only_when_asked(mt):
+    """mt_classify never times shapes (the kept shape stays the default); mt_classify_autotune
+    tunes the batch's class, reports the shape it used, keeps it for later calls, and every
+    call's outputs equal the oracle's."""
+    from helpers import compare_classify, oracle_params
+    c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=20_000)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    prm = dict(e_abs=31, e_permille=0, min_seeds=3, top_n=3, max_occ=1024)   # a class no other test tunes
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=8)
+    before = mt.eda_shape_for(0, True, 31)
+    assert before["tuned"] == 0
+    compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
+    assert mt.eda_shape_for(0, True, 31) == before
+    out = mt.classify_autotune(ix, r.seq, r.offsets, **prm)
+    compare_classify(out, ref)
+    sh = out["eda_shape"]
+    assert sh["tuned"] == 1 and sh["lanes_per_pair"] in (1, 2, 4, 8, 16, 32)
+    kept = mt.eda_shape_for(0, True, 31)
+    assert kept["tuned"] == 1 and kept["pairs_per_chunk"] == sh["pairs_per_chunk"] and kept["cta_threads"] == sh["cta_threads"]
+    compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
+    ix.close()

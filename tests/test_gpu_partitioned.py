@@ -225,3 +225,46 @@ def test_refused_calls(mt):
     with pytest.raises(mt.MtError):
         q.classify(one, **_prm(c))                  # not the kept list
     q.close()
+
+
+def test_more_batches_than_one_counting_pass_holds(mt):
+    """4,100 batches, more than the 4,096 indexes one counting pass takes: mt_part_contain_batches
+    makes a second pass for the last four, whose counters follow the first pass's. Every batch
+    holds one genome except the last, which also holds a copy of genome 7 (its count there is
+    merged with batch 7's by the highest-count rule). The per-genome counts equal one
+    mt_part_contain call per batch and the oracle's per-batch counts, on both sides of the
+    boundary."""
+    rng = np.random.default_rng(41)
+    G, L, k, w = 4100, 400, 21, 11
+    seq = gen.ascii_of(rng.integers(0, 4, G * L, dtype=np.uint8))
+    off = np.arange(G + 1, dtype=np.uint64) * np.uint64(L)
+    parts = [np.array([b], np.uint32) for b in range(G)]
+    parts[-1] = np.array([G - 1, 7], np.uint32)
+    # 1,220 reads of 100 bp: 300 from the genomes around the boundary, 20 from genome 7 (held by
+    # two batches), the rest anywhere
+    src = np.concatenate([rng.integers(4090, G, 300), np.full(20, 7), rng.integers(0, G, 900)])
+    reads = []
+    for gid in src:
+        p = int(rng.integers(0, L - 100))
+        r = seq[gid * L + p:gid * L + p + 100]
+        reads.append(gen.revcomp_ascii(r) if rng.random() < 0.5 else r)
+    r_seq = np.concatenate(reads)
+    r_off = np.arange(len(reads) + 1, dtype=np.uint64) * np.uint64(100)
+    dev = [mt.Index(*oracle.gather_genomes(seq, off, ids), k, w, 1) for ids in parts]
+    try:
+        q = mt.PartitionedQuery(G, r_seq, r_off)
+        q.contain_batches(dev, parts, max_occ=1024)
+        H = q.subset(1, 10000)["genome_hits"].astype(np.uint64)
+        q.close()
+        q = mt.PartitionedQuery(G, r_seq, r_off)
+        for ix, ids in zip(dev, parts):
+            q.contain(ix, ids, max_occ=1024)
+        H1 = q.subset(1, 10000)["genome_hits"].astype(np.uint64)
+        q.close()
+    finally:
+        for ix in dev:
+            ix.close()
+    ob = [(oracle.Index(*oracle.gather_genomes(seq, off, ids), k, w, 1), ids) for ids in parts]
+    H2 = oracle.partitioned_hits(ob, G, r_seq, r_off, 1024, threads=8)
+    assert np.array_equal(H, H2) and np.array_equal(H1, H2)
+    assert H[4096:].sum() > 0 and H[4090:4096].sum() > 0 and H[7] > 0

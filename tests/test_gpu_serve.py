@@ -101,7 +101,29 @@ def test_cancel_and_bounded_poll(mt, work):
     for rid in ids[:-1]:
         rc, _, out = srv.poll(rid, 120_000)
         assert rc == mt.MT_OK
-    assert srv.cancel(ids[0]) == mt.MT_EBUSY              # already done
+    assert srv.cancel(ids[0]) == mt.MT_EINVAL             # done, polled and released
+    rc, _, _ = srv.poll(ids[0], 0)
+    assert rc == mt.MT_EINVAL
+    srv.close()
+
+
+def test_server_releases_polled_requests(mt, work):
+    """The server keeps no request once a poll has reported its final status: a submitted,
+    finished and polled request's id is unknown afterwards, while an unpolled finished one still
+    answers, and cancelling a finished unpolled request is refused as busy."""
+    c, g, r, ix, prm = work
+    need = mt.workspace_bytes(ix, 3000 * 150, 3000, 150, **prm)
+    srv = mt.Server(ix, hbm_budget=4 * need, max_slots=1, **prm)
+    a = srv.submit(*_batch(r, 0, 3000))
+    b = srv.submit(*_batch(r, 3000, 6000))
+    rc, _, _ = srv.poll(b, 120_000)
+    assert rc == mt.MT_OK
+    assert srv.cancel(a) == mt.MT_EBUSY    # one slot, first in first out: a finished before b
+    rc, _, _ = srv.poll(a, 0)
+    assert rc == mt.MT_OK
+    for rid in (a, b):
+        assert mt.lib().mt_server_poll(srv._h, rid, 0, None) == mt.MT_EINVAL
+        assert srv.cancel(rid) == mt.MT_EINVAL
     srv.close()
 
 
