@@ -7,7 +7,8 @@ minimizers, index lookups, containment counts, locations, SneakySnake on every c
 the abundance profile. Inputs are resident in HBM when the timed region starts (1.5 GB of
 reads, larger than L2). `value` is reads/s of the batched form; the plain form, the
 end-to-end form with host buffers, the edit-distance stage alone on the batching workload
-(read-versus-window pairs) and a serving sample are reported beside it.
+(read-versus-window pairs), the serving workload (2,000 Poisson-arriving batches) and the
+large workload (6 Gb reference, a 10^7-read sub-batch) are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -31,17 +32,41 @@ sys.path.insert(0, ROOT)
 import gen  # noqa: E402
 
 METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact); p50/p99"
-# DRAM bytes (read + write) per read of the seeding kernel, from one ncu capture of the current
-# kernel on 2e6 reads of the same workload (dram__bytes_read.sum + dram__bytes_write.sum); the
-# index is fixed, so traffic grows in proportion to the reads. None whenever the kernel has
-# changed since the last capture.
-SEED_DRAM_BYTES_PER_READ = (7.053661e9 + 0.250544e9) / 2e6
-# Warp instructions per read of the seeding kernel (smsp__inst_executed.sum of the same capture,
-# 3.4526e9 on 2e6 reads); None whenever the kernel has changed since the last capture. The
-# kernel is bound by instruction issue, not DRAM: the issue roofline below uses it.
-SEED_WARP_INST_PER_READ = 3452561196 / 2e6
-WORKLOAD = ("medium: 200 genomes x 2 Mb (20 clades x 10, 1-10% divergence), k21 w11 canonical, "
-            "1e7 reads x 150 bp (both strands, 0.5% subst + 0.05% indel, 5% random), E=8, min_seeds 3, top 3")
+# Counters of the seeding kernel (k_seed) from one ncu capture of the bench command, per read:
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and warp instructions
+# (smsp__inst_executed.sum). They hold only for the kernel source they were taken on: its
+# files' SHA-256 is stored beside them, and the bench reports null for both whenever the
+# current source differs (the kernel changed since the capture).
+SEED_PROFILE = {"source_sha256": None, "dram_bytes_per_read": None, "warp_inst_per_read": None,
+                "capture": None}
+SEED_SOURCES = ("paper_2311_02029_gb300/csrc/classify.cu", "paper_2311_02029_gb300/csrc/common.cuh",
+                "paper_2311_02029_gb300/csrc/internal.h", "include/mt.h")
+
+
+def seed_source_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in SEED_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def seed_profile():
+    """(dram bytes per read, warp instructions per read) of the committed capture, or
+    (None, None) when the seeding kernel's sources have changed since it was taken."""
+    if SEED_PROFILE["source_sha256"] != seed_source_sha256():
+        return None, None
+    return SEED_PROFILE["dram_bytes_per_read"], SEED_PROFILE["warp_inst_per_read"]
+
+
+def workload_name(c: dict) -> str:
+    """The medium workload's description for its actual genome and read counts."""
+    return ("medium: %d genomes x 2 Mb (%d clades x 10, 1-10%% divergence), k21 w11 canonical, "
+            "%.3g reads x 150 bp (both strands, 0.5%% subst + 0.05%% indel, 5%% random), E=8, min_seeds 3, top 3"
+            % (c["n_genomes"], c["n_genomes"] // 10, c["n_reads"]))
+
+
 
 
 def log(*a):
@@ -167,7 +192,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "reads/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reads": c["n_reads"], "genomes": c["n_genomes"]},
+            "config": {"workload": workload_name(c), "reads": c["n_reads"], "genomes": c["n_genomes"]},
             "cpu_baseline": {"value": v, "unit": "reads/s", "cores": 1, "kind": "oracle",
                              "sample": "%d random reads of the workload per step (containment over the sample)" % S},
             "e2e": {"value": v, "unit": "reads/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -231,6 +256,7 @@ def large_workload(mt, torch, n_reads, steps, warmup, hbm):
     d_reads = torch.from_numpy(reads.seq).cuda()
     d_off = torch.from_numpy(reads.offsets.astype(np.int64)).cuda()
     stream = torch.cuda.current_stream()
+    eda_shape = mt.classify_autotune(ix, d_reads, d_off, **params(c, mt.MT_EDA_BATCHED))["eda_shape"]
     ms, outs = timed_steps(lambda: mt.classify(ix, d_reads, d_off, **params(c, mt.MT_EDA_BATCHED)),
                            steps, warmup, stream, torch)
     st = {k: statistics.mean(o["stats"][k] for o in outs) for k in outs[0]["stats"]}
@@ -246,6 +272,7 @@ def large_workload(mt, torch, n_reads, steps, warmup, hbm):
            "seed_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                              "algorithmic_bytes_per_launch": seed_bytes},
            "classified_frac": float((outs[-1]["taxon"] >= 0).float().mean().item()),
+           "eda_shape": eda_shape,
            "index": {"build_s": t_index, **info}, "data_s": t_data, "steps": steps, "warmup": warmup}
     del outs, d_reads, d_off
     ix.close()
@@ -276,6 +303,7 @@ def eda_stage(mt, torch, n_pairs, steps, warmup):
     stream = torch.cuda.current_stream()
     res = {}
     outs = {}
+    _, shapes = mt.eda_batch_autotune(rw, ro, ww, wo, pr, E)
     for name, mode in (("batched", mt.MT_EDA_BATCHED), ("plain", mt.MT_EDA_PLAIN)):
         ms, o = timed_steps(lambda: mt.eda_batch(rw, ro, ww, wo, pr, E, mode=mode), steps, warmup, stream, torch)
         res[name] = pairs.n_pairs / (ms / 1000.0)
@@ -287,6 +315,7 @@ def eda_stage(mt, torch, n_pairs, steps, warmup):
     # the other approximations on the same pairs, batched form
     others = {}
     for name, bits in EDA_OTHERS:
+        mt.eda_batch_autotune(rw, ro, ww, wo, pr, E, mode=bits | mt.MT_EDA_BATCHED)
         ms, o = timed_steps(lambda: mt.eda_batch(rw, ro, ww, wo, pr, E, mode=bits | mt.MT_EDA_BATCHED), steps,
                             warmup, stream, torch)
         others[name] = {"pairs_per_s": pairs.n_pairs / (ms / 1000.0), "ms": ms,
@@ -296,6 +325,8 @@ def eda_stage(mt, torch, n_pairs, steps, warmup):
             "pairs_per_s_batched": res["batched"], "pairs_per_s_plain": res["plain"],
             "ms_batched": res["ms_batched"], "ms_plain": res["ms_plain"],
             "batched_over_plain": res["batched"] / res["plain"], "identical": same,
+            "shapes_by_class": {"E %s" % rng: sh for rng, sh in zip(
+                ("0-1", "2-3", "4-7", "8-15", "16-31", "32-63", "64-127", "128+"), shapes) if sh["lanes_per_pair"]},
             "accepted_frac": accepted, "window_bases": window_bytes, "other_approximations": others}
 
 
@@ -398,7 +429,7 @@ def run_ours(args):
     _build.build()
     mt.lib()
 
-    c = gen.config(2, n_reads=args.reads)
+    c = gen.config(2, n_reads=args.reads, n_genomes=args.genomes)
     t0 = time.time()
     g = gen.make_genomes(c)
     reads = gen.make_reads(c, g, seed=c["seed"] + rank)
@@ -423,6 +454,9 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the approximation kernel's shape for this workload, timed once on the batch itself
+    # (mt_classify never times anything on its own)
+    eda_shape = mt.classify_autotune(ix, d_reads, d_off, **params(c, mt.MT_EDA_BATCHED))["eda_shape"]
     # batched form (the headline); clocks sampled during its timed region
     for _ in range(args.warmup):
         step(mt.MT_EDA_BATCHED)()
@@ -474,22 +508,32 @@ def run_ours(args):
     h_out = dict(taxon=pinned((n_reads,), np.int32), nloc=pinned((n_reads,), np.uint8),
                  locs=pinned((n_reads, top_n), mt.LOC_DTYPE), genome_hits=pinned((G,), np.uint64),
                  abundance=pinned((G,), np.float64))
+    # the classification's result (the problem statement's per-read taxon and abundance vector,
+    # with each read's location count and the per-genome hits); the per-read locations are an
+    # extra 72 bytes a read, measured beside it
+    h_res = dict(h_out, locs=None)
     e2e_ms, _ = timed_steps(lambda: mt.classify(ix, h_reads.numpy(), h_off.numpy().view(np.uint64),
-                                                out=h_out, **params(c, mt.MT_EDA_BATCHED)),
+                                                out=h_res, **params(c, mt.MT_EDA_BATCHED)),
                             max(1, args.steps // 2), 1, stream, torch)
+    e2e_locs_ms, _ = timed_steps(lambda: mt.classify(ix, h_reads.numpy(), h_off.numpy().view(np.uint64),
+                                                     out=h_out, **params(c, mt.MT_EDA_BATCHED)),
+                                 max(1, args.steps // 2), 1, stream, torch)
     e2e_graph_ms, _ = timed_steps(lambda: plan.classify(h_reads.numpy(), h_off.numpy().view(np.uint64), out=h_out),
                                   max(1, args.steps // 2), 1, stream, torch)
     plan.close()
     e2e_ms = max_over_ranks(e2e_ms, world)
+    e2e_locs_ms = max_over_ranks(e2e_locs_ms, world)
     e2e_graph_ms = max_over_ranks(e2e_graph_ms, world)
     h2d = n_bases + (n_reads + 1) * 8
-    d2h = n_reads * (4 + 1 + 24 * top_n) + G * 16
+    d2h = n_reads * (4 + 1) + G * 16
+    d2h_locs = d2h + n_reads * 24 * top_n
 
     # whole classification with each other approximation (batched form, same inputs)
     approx = {}
     if rank == 0 and world == 1:
         for name, bits in EDA_OTHERS:
             prm = dict(params(c, mt.MT_EDA_BATCHED), eda_mode=bits | mt.MT_EDA_BATCHED)
+            mt.classify_autotune(ix, d_reads, d_off, **prm)
             fn = lambda: mt.classify(ix, d_reads, d_off, **prm)  # noqa: E731
             ms_a, o = timed_steps(fn, max(1, args.steps // 2), 1, stream, torch)
             sa = o[-1]["stats"]
@@ -582,16 +626,18 @@ def run_ours(args):
     # instruction issue: one warp instruction per cycle per scheduler, 4 schedulers per SM, at
     # the SM clock sampled during the timed region (the maximum clock when none was sampled)
     issue = None
-    if SEED_WARP_INST_PER_READ:
+    seed_dram_per_read, seed_inst_per_read = seed_profile()
+    if seed_inst_per_read:
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
         peak_issue = sms * 4 * mhz * 1e6 / 1e9
-        got_issue = SEED_WARP_INST_PER_READ * n_reads / (st["ms_seed"] / 1000.0) / 1e9
+        got_issue = seed_inst_per_read * n_reads / (st["ms_seed"] / 1000.0) / 1e9
         issue = {"achieved": got_issue, "peak": peak_issue, "unit": "G warp instructions/s",
-                 "frac": got_issue / peak_issue, "warp_instructions_per_read": SEED_WARP_INST_PER_READ,
+                 "frac": got_issue / peak_issue, "warp_instructions_per_read": seed_inst_per_read,
                  "peak_kind": "%d SMs x 4 schedulers x 1 instruction/cycle x %.0f MHz (sampled SM clock)" % (sms, mhz)}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": (SEED_DRAM_BYTES_PER_READ * n_reads if SEED_DRAM_BYTES_PER_READ else None),
+                "traffic": (seed_dram_per_read * n_reads if seed_dram_per_read else None),
+                "traffic_capture": SEED_PROFILE["capture"] if seed_dram_per_read else None,
                 "kernel": "k_seed",
                 "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind,
                 "algorithmic_bytes_per_launch": seed_bytes, "ms_per_launch": st["ms_seed"],
@@ -613,7 +659,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded generator; the paper's CAMI reads "
                                                             "and NCBI database are not available)",
-            "config": {"workload": WORKLOAD, "reads": n_reads, "genomes": g.n, "reference_bases": int(g.offsets[-1]),
+            "config": {"workload": workload_name(c), "reads": n_reads, "genomes": g.n, "reference_bases": int(g.offsets[-1]),
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (%.2f GB reads, %.2f GB index)" % (n_bases / 1e9, info["device_bytes"] / 1e9)},
             "pairs_per_s": st["n_candidates"] / (ms / 1000.0) * world,
@@ -623,8 +669,12 @@ def run_ours(args):
                       "e2e_value": job_rate(n_reads, world, e2e_graph_ms), "e2e_ms_per_step": e2e_graph_ms},
             "roofline": roofline,
             "e2e": {"value": job_rate(n_reads, world, e2e_ms), "unit": "reads/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "result": "per-read taxon and location count, per-genome hits and abundances (pinned host arrays)",
+                    "with_locations": {"value": job_rate(n_reads, world, e2e_locs_ms), "ms_per_step": e2e_locs_ms,
+                                       "d2h_bytes_per_step": d2h_locs}},
             "clocks": clocks, "gpu_launches": int(st["n_launches"]) * args.steps,
+            "eda_shape": eda_shape,
             "index": {"build_s": index_s, **info},
             "classified_frac": float((batched_out["taxon"] >= 0).float().mean().item()),
             "other_approximations": approx,
@@ -678,12 +728,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--reads", type=int, default=gen.CONFIGS[2]["n_reads"])
+    ap.add_argument("--genomes", type=int, default=gen.CONFIGS[2]["n_genomes"],
+                    help="genomes of the medium reference (clades of 10); fewer make a small profiling case")
     ap.add_argument("--eda-pairs", type=int, default=gen.CONFIGS[3]["n_pairs"])
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=100.0,
+                    help="seconds of serving arrivals (20 batches/s; 100 s = the workload's 2,000 batches)")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--part-batches", type=int, default=25)
-    ap.add_argument("--large-reads", type=int, default=0,
-                    help="also time the large workload (6 Gb reference) on a sub-batch of this many reads")
+    ap.add_argument("--large-reads", type=int, default=10_000_000,
+                    help="time the large workload (6 Gb reference) on a sub-batch of this many reads (0: skip)")
     ap.add_argument("--ref-sample", type=int, default=20_000)
     args = ap.parse_args()
     if args.warmup < 3:
