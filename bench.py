@@ -37,8 +37,13 @@ METRIC = "reads/s and candidate pairs/s at 1 GB300 (batched vs plain, bit-exact)
 # (smsp__inst_executed.sum). They hold only for the kernel source they were taken on: its
 # files' SHA-256 is stored beside them, and the bench reports null for both whenever the
 # current source differs (the kernel changed since the capture).
-SEED_PROFILE = {"source_sha256": None, "dram_bytes_per_read": None, "warp_inst_per_read": None,
-                "capture": None}
+SEED_PROFILE = {"source_sha256": "8b2f25f2851841c9251a13b8a5db79350dc26a1e466c95bdccd4364e49d0ef18",
+                "dram_bytes_per_read": (35508836608 + 1278109952) / 1e7,
+                "warp_inst_per_read": 13762556818 / 1e7,
+                "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,smsp__inst_executed.sum,"
+                           "gpu__time_duration.sum --clock-control none -k regex:k_seed -s 4 -c 1 (1 pass) on "
+                           "python bench.py --steps 3 --warmup 3 --eda-pairs 0 --serve-seconds 0 --cpu-sample 0 "
+                           "--part-batches 0 --large-reads 0 (the medium workload, 10^7 reads)"}
 SEED_SOURCES = ("paper_2311_02029_gb300/csrc/classify.cu", "paper_2311_02029_gb300/csrc/common.cuh",
                 "paper_2311_02029_gb300/csrc/internal.h", "include/mt.h")
 
