@@ -911,17 +911,26 @@ __global__ void k_mask(const unsigned long long *hits, uint32_t G, uint32_t num,
 }
 
 // ---- candidate selection ----------------------------------------------------------------------
+// A tile's candidates enter the compact list ordered by seed count (most seeds first, a
+// counting sort over 64 bins in shared memory): a location holding nearly all of a read's seeds
+// is usually a near-exact match whose approximation ends in a step or two, one holding few is
+// usually a divergent genome walked to E + 1 obstacles, so a warp of the approximation kernel
+// that takes consecutive candidates walks them for similar numbers of steps. The order of the
+// list changes no result (each distance goes to its candidate's slot).
 __global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep,
                          uint32_t top_n, Cluster *cand, uint8_t *nloc_ws, uint32_t *cl, uint32_t *fb_list,
                          Counters *ctr) {
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    __shared__ uint32_t s_warp[32];
+    constexpr uint32_t BINS = 64;
+    __shared__ uint32_t s_bin[BINS];
     __shared__ unsigned long long s_base;
     const uint64_t n_reads = io->n_reads;
     for (uint64_t r0 = (uint64_t)blockIdx.x * blockDim.x; r0 < n_reads; r0 += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t r = r0 + threadIdx.x;
         uint32_t taken = 0;
+        uint64_t bins = 0;       // bin of candidate t in bits 6t .. 6t+5
         bool fb = false;
+        if (threadIdx.x < BINS) s_bin[threadIdx.x] = 0;
+        __syncthreads();
         if (r < n_reads) {
             uint32_t q = qcnt[r];
             if (q == QOVF) {
@@ -931,7 +940,11 @@ __global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster 
                 uint32_t lim = min(q, CSTORE);
                 for (uint32_t i = 0; i < lim && taken < top_n; i++) {
                     Cluster c = clus[r * CSTORE + i];
-                    if (keep[hk_genome(c.hkey)]) cand[r * top_n + taken++] = c;
+                    if (keep[hk_genome(c.hkey)]) {
+                        const uint32_t bin = BINS - 1 - min(c.seeds, BINS - 1);
+                        bins |= (uint64_t)bin << (6 * taken);
+                        cand[r * top_n + taken++] = c;
+                    }
                 }
                 if (taken < top_n && q > CSTORE) { fb = true; taken = 0; }
                 nloc_ws[r] = (uint8_t)taken;
@@ -941,23 +954,25 @@ __global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster 
             unsigned long long slot = atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->fb_count), 1ull);
             fb_list[slot] = (uint32_t)r;
         }
-        // compact candidate slots: one counter update per block and tile
-        const uint32_t incl = warp_incl_scan(taken);
-        if (lane == 31) s_warp[warp] = incl;
+        for (uint32_t t = 0; t < taken; t++) atomicAdd(&s_bin[(bins >> (6 * t)) & (BINS - 1)], 1u);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t run = 0;
-            for (uint32_t i = 0; i < blockDim.x / 32; i++) {
-                const uint32_t t = s_warp[i];
-                s_warp[i] = run;
-                run += t;
-            }
-            s_base = run ? atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->cl_count), (unsigned long long)run) : 0;
+        if (threadIdx.x < 32) {   // bin starts within the tile, and the tile's place in the list
+            const uint32_t lane = threadIdx.x;
+            const uint32_t c0 = s_bin[2 * lane], c1 = s_bin[2 * lane + 1];
+            const uint32_t incl = warp_incl_scan(c0 + c1);
+            const uint32_t run = __shfl_sync(FULL, incl, 31);
+            s_bin[2 * lane] = incl - c0 - c1;
+            s_bin[2 * lane + 1] = incl - c1;
+            if (lane == 0)
+                s_base = run ? atomicAdd(reinterpret_cast<unsigned long long *>(&ctr->cl_count), (unsigned long long)run) : 0;
         }
         __syncthreads();
-        const unsigned long long base = s_base + s_warp[warp];
-        for (uint32_t t = 0; t < taken; t++) cl[base + incl - taken + t] = (uint32_t)(r * top_n + t);
-        __syncthreads();   // s_warp and s_base are reused by the next tile
+        const unsigned long long base = s_base;
+        for (uint32_t t = 0; t < taken; t++) {
+            const uint32_t pos = atomicAdd(&s_bin[(bins >> (6 * t)) & (BINS - 1)], 1u);
+            cl[base + pos] = (uint32_t)(r * top_n + t);
+        }
+        __syncthreads();   // s_bin and s_base are reused by the next tile
     }
 }
 
