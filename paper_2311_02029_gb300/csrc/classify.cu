@@ -17,6 +17,7 @@
 //   k_decide   (stage 3a)  per-read decision, unique counts, multi-mapped reads.
 //   k_multi / k_abund (stage 3a-b) multi-read split, relative abundances, 0.01% cutoff.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -49,14 +50,15 @@ static constexpr int FB_CTAS = 16;
 static constexpr int FB_THREADS = 256;
 
 // Per-warp shared memory of the seeding kernel. HitT is the seed-match key: 32 bits when the
-// index's genome count and lengths allow (see HitKey), else 64.
-template <typename HitT>
+// index's genome count and lengths allow (see HitKey), else 64. The w = 11 block path keeps no
+// per-position keys (W11: key[] shrinks to one word).
+template <typename HitT, bool W11 = false>
 struct WarpSmem {
     uint64_t rd[RDW];               // packed read
     HitT hits[HCAP];                // seed-match keys of the read
     union {                         // the tiles of a read, then its location walk
         struct {
-            uint64_t key[KEYS];     // k-mer keys of the tile
+            uint64_t key[W11 ? 1 : KEYS];   // k-mer keys of the tile (general path)
             uint64_t code[KEYS];    // canonical code | strand << 63
             uint16_t mpos[MPOS];    // minimizer positions of the tile
             // lookups of one round, by rank among those with matches
@@ -389,8 +391,8 @@ MT_DEV uint32_t mix64_hi(uint64_t z) {
 // share them and the window is redone on full 64-bit keys. Appends the selected positions
 // (absolute, each once) to mpos and returns their number; carry is the selection of the
 // previous pass's last window (-1 before the first pass).
-template <typename HitT>
-MT_DEV uint32_t minimizers_w11(WarpSmem<HitT> &ws, uint32_t t0, uint32_t tw, uint32_t k, uint32_t canonical,
+template <typename WS>
+MT_DEV uint32_t minimizers_w11(WS &ws, uint32_t t0, uint32_t tw, uint32_t k, uint32_t canonical,
                                int32_t &carry) {
     const uint32_t lane = lane_id();
     const uint32_t b = 5u * lane;                 // first local position of this lane
@@ -482,6 +484,36 @@ MT_DEV uint32_t minimizers_w11(WarpSmem<HitT> &ws, uint32_t t0, uint32_t tw, uin
 // COUNT: containment only (every occurrence of every minimizer counted per genome, no
 // locations, no outputs per read); HPC: the reads' seeds are taken after homopolymer
 // compression (an index built with MT_INDEX_HPC).
+// Adds c seed hits of genome g into the CTA's 32-bit shared counter (or straight to the 64-bit
+// global counter). CHECKED adds (the per-occurrence counting of containment and of overflowing
+// reads, which max_occ alone does not bound) move the counter to the global one once it reaches
+// 2^31; unchecked adds come from the location walk, at most HCAP a read, so a CTA's share of a
+// launch (fewer than 2^32 / MT_MAX_TOPN reads over at least min(reads / 8, SMs) CTAs) adds under
+// 2^28 a genome: the counter never wraps.
+template <bool SMEM_HIST, bool CHECKED>
+MT_DEV void add_hits(uint32_t *hist, unsigned long long *ghits, uint32_t g, uint32_t c) {
+    if (SMEM_HIST) {
+        if (CHECKED) {
+            const uint32_t old = atomicAdd(&hist[g], c);
+            if (old + c >= 0x80000000u) {
+                const uint32_t v = atomicExch(&hist[g], 0u);
+                if (v) atomicAdd(&ghits[g], (unsigned long long)v);
+            }
+        } else {
+            atomicAdd(&hist[g], c);
+        }
+    } else {
+        atomicAdd(&ghits[g], (unsigned long long)c);
+    }
+}
+
+// Shared memory of one seeding CTA: 32-bit genome counters, then the warps' areas.
+template <bool HK32, bool W11>
+static size_t seed_smem_bytes(uint32_t hist_n) {
+    using HitT = typename std::conditional<HK32, uint32_t, uint64_t>::type;
+    return (((size_t)hist_n * 4 + 15) & ~(size_t)15) + SEED_WARPS * sizeof(WarpSmem<HitT, W11>);
+}
+
 // W11: the index has w = 11 and k <= 28, and the minimizers come from the block path
 // (minimizers_w11); otherwise the general window-minimum path runs.
 template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false, bool W11 = false>
@@ -490,16 +522,16 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
     static_assert(!(MULTI && W11), "the block path keeps no keys for several tables");
     using HitT = typename HitKey<HK32>::T;
     extern __shared__ __align__(16) unsigned char smraw[];
-    unsigned long long *hist = reinterpret_cast<unsigned long long *>(smraw);
+    using WS = WarpSmem<HitT, W11>;
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smraw);
     const uint32_t hist_n = SMEM_HIST ? (MULTI ? A.n_hist : A.ix.G) : 0;
-    WarpSmem<HitT> *wsall = reinterpret_cast<WarpSmem<HitT> *>(smraw + ((hist_n * 8 + 15) & ~15u));
+    WS *wsall = reinterpret_cast<WS *>(smraw + ((hist_n * 4 + 15) & ~15u));
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    WarpSmem<HitT> &ws = wsall[warp];
+    WS &ws = wsall[warp];
     if (SMEM_HIST) {
         for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x) hist[g] = 0;
         __syncthreads();
     }
-    unsigned long long *H_out = SMEM_HIST ? hist : A.ghits;
     const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
     HitKey<HK32> hf;
     hf.db = A.ix.hk_db;
@@ -700,7 +732,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                         if (ni && cnt) {
 #pragma unroll
                             for (uint32_t t = 0; t < 3; t++)
-                                if (t < cnt) atomicAdd(&H_out[base + ((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33)], 1ull);
+                                if (t < cnt) add_hits<SMEM_HIST, true>(hist, A.ghits, base + (uint32_t)((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33), 1u);
                         }
                         unsigned ext = __ballot_sync(FULL, ni == 0 && cnt != 0);
                         while (ext) {
@@ -710,7 +742,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                             const uint32_t bb = __shfl_sync(FULL, base, src);
                             const uint64_t off = __shfl_sync(FULL, w1 & OFF_MASK40, src);
                             const uint64_t *oc = (const uint64_t *)__shfl_sync(FULL, (unsigned long long)occ, src);
-                            for (uint32_t q = lane; q < c; q += 32) atomicAdd(&H_out[bb + (__ldg(&oc[off + q]) >> 33)], 1ull);
+                            for (uint32_t q = lane; q < c; q += 32) add_hits<SMEM_HIST, true>(hist, A.ghits, bb + (uint32_t)(__ldg(&oc[off + q]) >> 33), 1u);
                         }
                     }
                     // keep the unprobed tail (fewer than 32) at the front of the queue
@@ -759,7 +791,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                 const uint32_t pre = incl - cnt;
                 if (!ovf && H + total > HCAP) {
                     // switch to counting only: count what is buffered so far
-                    for (uint32_t i = lane; i < H; i += 32) atomicAdd(&H_out[hf.genome(ws.hits[i])], 1ull);
+                    for (uint32_t i = lane; i < H; i += 32) add_hits<SMEM_HIST, true>(hist, A.ghits, hf.genome(ws.hits[i]), 1u);
                     ovf = true;
                 }
                 if (!ovf) {
@@ -792,7 +824,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                     if (ni && cnt) {
 #pragma unroll
                         for (uint32_t t = 0; t < 3; t++)
-                            if (t < cnt) atomicAdd(&H_out[(t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33], 1ull);
+                            if (t < cnt) add_hits<SMEM_HIST, true>(hist, A.ghits, (uint32_t)((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33), 1u);
                     }
                     unsigned ext = __ballot_sync(FULL, ni == 0 && cnt != 0);
                     while (ext) {
@@ -800,7 +832,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                         ext &= ext - 1;
                         const uint32_t c = __shfl_sync(FULL, cnt, src);
                         const uint64_t off = __shfl_sync(FULL, w1 & OFF_MASK40, src);
-                        for (uint32_t q = lane; q < c; q += 32) atomicAdd(&H_out[__ldg(&A.ix.occ[off + q]) >> 33], 1ull);
+                        for (uint32_t q = lane; q < c; q += 32) add_hits<SMEM_HIST, true>(hist, A.ghits, (uint32_t)(__ldg(&A.ix.occ[off + q]) >> 33), 1u);
                     }
                 }
                 __syncwarp();
@@ -839,7 +871,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
         for (uint32_t gi = lane; gi < ng; gi += 32) {
             uint32_t s = ws.u.wk.gs[gi];
             const uint32_t ge = ws.u.wk.gs[gi + 1];
-            atomicAdd(&H_out[hf.genome(ws.hits[s])], (unsigned long long)(ge - s));
+            add_hits<SMEM_HIST, false>(hist, A.ghits, hf.genome(ws.hits[s]), ge - s);
             while (s < ge) {
                 const uint32_t e = lower_bound_t<HitT>(ws.hits, s + 1, ge, (HitT)(ws.hits[s] + E + 1));
                 if (e - s >= A.min_seeds) {
@@ -881,7 +913,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
     if (SMEM_HIST) {
         __syncthreads();
         for (uint32_t g = threadIdx.x; g < hist_n; g += blockDim.x)
-            if (hist[g]) atomicAdd(&A.ghits[g], hist[g]);
+            if (hist[g]) atomicAdd(&A.ghits[g], (unsigned long long)hist[g]);
     }
 }
 
@@ -1618,7 +1650,10 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
         A.ctr = ctr;
         const bool smem_hist = G <= SMEM_HIST_MAX;
         const bool hk32 = ix->hk_db != 0;
-        const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * (hk32 ? sizeof(WarpSmem<uint32_t>) : sizeof(WarpSmem<uint64_t>));
+        const uint32_t hist_n = smem_hist ? G : 0;
+        const bool w11 = seed_w11(ix);
+        const size_t smem = hk32 ? (w11 ? seed_smem_bytes<true, true>(hist_n) : seed_smem_bytes<true, false>(hist_n))
+                                 : (w11 ? seed_smem_bytes<false, true>(hist_n) : seed_smem_bytes<false, false>(hist_n));
         auto seed = [&](uint64_t rb, uint64_t re) {
             A.r_begin = rb;
             A.r_end = re;
@@ -2025,7 +2060,8 @@ extern "C" int mt_containment(const mt_index *ix, const uint8_t *reads, uint64_t
         A.r_begin = 0;
         A.r_end = ~0ull;
         const bool smem_hist = G <= SMEM_HIST_MAX;
-        const size_t smem = (smem_hist ? ((G * 8 + 15) & ~15u) : 0) + SEED_WARPS * sizeof(WarpSmem<uint64_t>);
+        const size_t smem = (!ix->hpc && seed_w11(ix)) ? seed_smem_bytes<false, true>(smem_hist ? G : 0)
+                                                       : seed_smem_bytes<false, false>(smem_hist ? G : 0);
         const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
         if (ix->hpc) rc = smem_hist ? launch_seed<true, false, true, true>(A, smem, need, s)
                                     : launch_seed<false, false, true, true>(A, smem, need, s);
@@ -2116,7 +2152,7 @@ int mt::contain_multi(const mt_index *const *batches, uint32_t n_batches, const 
         A.n_hist = (uint32_t)T;
         A.div_magic = n_batches > 1 ? (uint32_t)(((1ull << 32) + n_batches - 1) / n_batches) : 0u;
         const bool smem_hist = T <= SMEM_HIST_MAX;
-        const size_t smem = (smem_hist ? ((T * 8 + 15) & ~15ull) : 0) + SEED_WARPS * sizeof(WarpSmem<uint64_t>);
+        const size_t smem = seed_smem_bytes<false, false>(smem_hist ? (uint32_t)T : 0);
         const uint64_t need = (n_reads + SEED_WARPS - 1) / SEED_WARPS;
         if (b0->hpc) rc = smem_hist ? launch_seed<true, false, true, true, true>(A, smem, need, s)
                                     : launch_seed<false, false, true, true, true>(A, smem, need, s);
