@@ -266,6 +266,16 @@ def large_workload(mt, torch, n_reads, steps, warmup, hbm):
                            steps, warmup, stream, torch)
     st = {k: statistics.mean(o["stats"][k] for o in outs) for k in outs[0]["stats"]}
     n_bases = int(reads.offsets[-1])
+    # the same batch through a preallocated plan replayed from its captured CUDA graph
+    plan = mt.Plan(ix, max_reads=reads.n, max_bases=n_bases, max_read_len=int(reads.lengths.max()),
+                   **params(c, mt.MT_EDA_BATCHED))
+    ms_graph, gouts = timed_steps(lambda: plan.classify(d_reads, d_off), steps, warmup, stream, torch)
+    graph_identical = (torch.equal(outs[-1]["taxon"], gouts[-1]["taxon"])
+                       and torch.equal(outs[-1]["locs"], gouts[-1]["locs"])
+                       and torch.equal(outs[-1]["genome_hits"], gouts[-1]["genome_hits"])
+                       and bool((outs[-1]["abundance"] - gouts[-1]["abundance"]).abs().max().item() <= 1e-6))
+    plan.close()
+    del gouts
     seed_bytes = (n_bases + 2 * (n_bases / 32.0 + reads.n) * 8 + st["n_minimizers"] * (32 + 32)
                   + st["n_hits"] * 16 * 2)
     achieved = seed_bytes / (st["ms_seed"] / 1000.0) / 1e9
@@ -273,6 +283,9 @@ def large_workload(mt, torch, n_reads, steps, warmup, hbm):
                        "%d reads (60%% 150 bp, 40%% 250 bp), E = 5%% of n, min_seeds 3, top 3" % reads.n,
            "reads_per_s": reads.n / (ms / 1000.0), "ms_per_step": ms,
            "pairs_per_s": st["n_candidates"] / (ms / 1000.0),
+           "graph": {"reads_per_s": reads.n / (ms_graph / 1000.0), "ms_per_step": ms_graph,
+                     "identical": graph_identical,
+                     "form": "batched persistent path, preallocated plan replayed from its captured CUDA graph"},
            "stage_ms": {k[3:]: st[k] for k in ("ms_seed", "ms_select", "ms_eda", "ms_profile", "ms_total")},
            "seed_roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                              "algorithmic_bytes_per_launch": seed_bytes},
