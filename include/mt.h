@@ -229,7 +229,7 @@ typedef struct {
     uint32_t cta_threads;       /* threads per CTA of the persistent launch (128 .. 1024) */
     uint32_t refill;            /* SneakySnake, one lane per pair: 1 = a lane takes a new pair as
                                    soon as its own ends; 0 = the warp's lanes take pairs together */
-    uint32_t tuned;             /* 1: chosen by an autotune call in this process; 0: the default */
+    uint32_t tuned;             /* 1: kept in this process (an autotune call or mt_eda_set_shape); 0: the default */
 } mt_eda_shape;
 
 /* mt_classify that first times the batched approximation kernel's shapes on this batch's own
@@ -247,9 +247,16 @@ int mt_classify_autotune(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
 
 /* The shape the batched approximation kernel uses on this device for approximation `mode`
  * (form bits ignored), pairs of edit threshold E, in classification (classification = 1) or in
- * mt_eda_batch (0): the tuned one if an autotune call chose it, else the default.
- * Errors: MT_EINVAL, MT_ECUDA. */
+ * mt_eda_batch (0): the kept one if an autotune call chose it or mt_eda_set_shape set it
+ * (tuned = 1), else the default (tuned = 0). Errors: MT_EINVAL, MT_ECUDA. */
 int mt_eda_shape_for(uint32_t mode, int classification, uint32_t E, mt_eda_shape *out);
+/* Keeps `shape` for the edit-threshold class of E (as an autotune call would), e.g. a shape
+ * tuned in an earlier process and stored by the caller. Valid shapes: lanes_per_pair a power
+ * of two up to 32 (32 for q-gram), pairs_per_chunk 1..4096, cta_threads a multiple of 32 up to
+ * 1024, refill 0 or 1 (1 only for SneakySnake with one lane per pair); `tuned` is ignored.
+ * lanes_per_pair = 0 forgets the kept shape (the class runs the default again). Every shape
+ * gives the same distances. Errors: MT_EINVAL (an invalid shape or argument), MT_ECUDA. */
+int mt_eda_set_shape(uint32_t mode, int classification, uint32_t E, const mt_eda_shape *shape);
 
 /* ---- containment alone (Fig. 1 stage 1; "The MetaTrinity Pipeline") ------------------------
  * Seed hits per genome over the batch, counted with multiplicity for every minimizer of every

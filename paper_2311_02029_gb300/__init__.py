@@ -103,7 +103,7 @@ EXPORTS = ["mt_strerror", "mt_last_cuda_error", "mt_version", "mt_build_index", 
            "mt_server_cancel", "mt_server_destroy", "mt_part_create", "mt_part_contain", "mt_part_contain_batches", "mt_part_subset",
            "mt_part_classify", "mt_part_destroy", "mt_classify_partitioned", "mt_classify_genome_sharded",
            "mt_inject_alloc_failure", "mt_pool_used_bytes", "mt_classify_autotune", "mt_eda_batch_autotune",
-           "mt_eda_shape_for", "mt_profile_rollup_device"]
+           "mt_eda_shape_for", "mt_eda_set_shape", "mt_profile_rollup_device"]
 
 
 def lib():
@@ -150,6 +150,8 @@ def lib():
         L.mt_eda_batch_autotune.argtypes = [vp, vp, u64, vp, vp, vp, vp, u64, u32, vp, vp, vp]
         L.mt_eda_shape_for.restype = i32
         L.mt_eda_shape_for.argtypes = [u32, i32, u32, ctypes.POINTER(EdaShape)]
+        L.mt_eda_set_shape.restype = i32
+        L.mt_eda_set_shape.argtypes = [u32, i32, u32, ctypes.POINTER(EdaShape)]
         L.mt_classify_masked.restype = i32
         L.mt_classify_masked.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(ClassifyParams), i32, vp,
                                          vp, vp, vp, vp, vp, vp, ctypes.POINTER(Stats)]
@@ -405,6 +407,14 @@ def eda_shape_for(mode: int, classification: bool, E: int) -> dict:
     sh = EdaShape()
     _check(lib().mt_eda_shape_for(mode, 1 if classification else 0, E, ctypes.byref(sh)), "mt_eda_shape_for")
     return sh.as_dict()
+
+
+def eda_set_shape(mode: int, classification: bool, E: int, lanes_per_pair: int, pairs_per_chunk: int = 128,
+                  cta_threads: int = 256, refill: int = 0):
+    """``mt_eda_set_shape``: keep a shape for approximation ``mode`` and E's class (e.g. one tuned
+    in an earlier process); ``lanes_per_pair=0`` forgets it."""
+    sh = EdaShape(lanes_per_pair, pairs_per_chunk, cta_threads, refill, 1)
+    _check(lib().mt_eda_set_shape(mode, 1 if classification else 0, E, ctypes.byref(sh)), "mt_eda_set_shape")
 
 
 def classify_masked(ix: Index, reads, offsets, keep, *, stream=None, want_locs=True, out=None, **params) -> dict:

@@ -844,6 +844,23 @@ extern "C" int mt_eda_batch_autotune(const uint64_t *read_words, const uint64_t 
                           dist, (mode & 15u) == MT_EDA_BATCHED, shapes);
 }
 
+extern "C" int mt_eda_set_shape(uint32_t mode, int classification, uint32_t E, const mt_eda_shape *shape) {
+    if (!shape || !eda_mode_ok(mode) || E > MT_MAX_E) return MT_EINVAL;
+    const int algo = (int)(mode >> 4);
+    const uint32_t G = shape->lanes_per_pair, ch = shape->pairs_per_chunk, cta = shape->cta_threads;
+    TunedShape t{0, 0, 0, 0};   // lanes_per_pair = 0: forget the kept shape
+    if (G) {
+        if (G > 32 || (G & (G - 1)) || (algo == ALGO_QGRAM && G != 32)) return MT_EINVAL;
+        if (ch == 0 || ch > 4096 || cta < 32 || cta > (uint32_t)EDA_MAX_THREADS || cta % 32) return MT_EINVAL;
+        if (shape->refill > 1 || (shape->refill && (algo != ALGO_SNAKE || G != 1))) return MT_EINVAL;
+        t = TunedShape{G, ch, cta, shape->refill};
+    }
+    int dev = 0;
+    if (!cuda_ok(cudaGetDevice(&dev), "cudaGetDevice")) return MT_ECUDA;
+    set_tuned_shape(dev, algo, (classification ? MAX_CLASSES : 0) + e_class(E), t);
+    return MT_OK;
+}
+
 extern "C" int mt_eda_shape_for(uint32_t mode, int classification, uint32_t E, mt_eda_shape *out) {
     if (!out || !eda_mode_ok(mode) || E > MT_MAX_E) return MT_EINVAL;
     int dev = 0;

@@ -214,6 +214,12 @@ def test_every_entry_point_refuses_null_arguments_without_gpu(mtlib):
     sh = mtlib.EdaShape()
     assert L.mt_eda_shape_for(0x70, 0, 8, ctypes.byref(sh)) == E                     # no such approximation
     assert L.mt_eda_shape_for(0, 0, 200, ctypes.byref(sh)) == E                      # E above MT_MAX_E
+    for bad in ((3, 128, 256, 0), (64, 128, 256, 0), (1, 0, 256, 0), (1, 128, 2048, 0),
+                (1, 128, 100, 0), (2, 128, 256, 1), (1, 128, 256, 2)):
+        assert L.mt_eda_set_shape(0, 0, 8, ctypes.byref(mtlib.EdaShape(*bad, 1))) == E, bad
+    assert L.mt_eda_set_shape(0x30, 1, 8, ctypes.byref(mtlib.EdaShape(1, 128, 256, 0, 1))) == E   # q-gram: 32 lanes
+    assert L.mt_eda_set_shape(0x10, 1, 8, ctypes.byref(mtlib.EdaShape(1, 128, 256, 1, 1))) == E   # refill: SneakySnake only
+    assert L.mt_eda_set_shape(0, 0, 8, None) == E
     assert L.mt_eda_batch_autotune(p, p, 1, p, p, p, p, 1, 99, None, p, None) == E   # no such form
     assert L.mt_classify_autotune(None, p, 8, p, 1, ctypes.byref(cp), 0, None, p, p, p, p, p, ctypes.byref(st),
                                   ctypes.byref(sh)) == E

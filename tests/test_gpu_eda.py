@@ -182,3 +182,88 @@ def test_classify_tunes_only_when_asked(mt):
     assert kept["tuned"] == 1 and kept["pairs_per_chunk"] == sh["pairs_per_chunk"] and kept["cta_threads"] == sh["cta_threads"]
     compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
     ix.close()
+
+
+def _all_class_pairs(seed):
+    """Pairs of every edit-threshold class ([0,1] ... [64,127]) and lengths 1 to 1024, half of
+    them within a few substitutions of a window offset."""
+    rng = np.random.default_rng(seed)
+    reads, wins, Es = [], [], []
+    for i in range(700):
+        n = int(rng.choice([1, 5, 32, 33, 150, 251, 1024]))
+        E = int(rng.choice([0, 1, 2, 3, 4, 7, 8, 15, 16, 31, 32, 63, 64, 127]))
+        r = gen.ascii_of(rng.integers(0, 4, n, dtype=np.uint8))
+        w = gen.ascii_of(rng.integers(0, 4, n + 2 * E, dtype=np.uint8))
+        if i % 2:
+            s = int(rng.integers(0, 2 * E + 1))
+            w[s:s + n] = r
+            for _ in range(int(rng.integers(0, 5))):
+                j = s + int(rng.integers(0, n))
+                w[j] = ord("A") if w[j] != ord("A") else ord("T")
+        reads.append(r)
+        wins.append(w)
+        Es.append(E)
+    return gen.EdaPairs(read_seq=np.concatenate(reads), read_off=np.cumsum([0] + [len(x) for x in reads]).astype(np.uint64),
+                        win_seq=np.concatenate(wins), win_off=np.cumsum([0] + [len(x) for x in wins]).astype(np.uint64),
+                        pair_read=np.arange(len(reads), dtype=np.uint32), E=np.array(Es, np.uint16),
+                        planted=np.zeros(len(reads), np.uint16))
+
+
+CLASS_E = [0, 2, 4, 8, 16, 32, 64]          # one edit threshold of each class that can occur
+ALGO_BITS = [(0x00, 0), (0x10, 1), (0x20, 2), (0x30, 3), (0x40, 4)]
+
+
+def _shapes(bits):
+    if bits == 0x30:                          # q-gram: a whole warp per pair
+        lanes = [(32, 0)]
+    else:
+        lanes = [(G, 0) for G in (1, 2, 4, 8, 16, 32)] + ([(1, 1)] if bits == 0 else [])
+    return [(G, ch, cta, rf) for G, rf in lanes for ch, cta in ((1, 32), (7, 96), (128, 256), (4096, 1024))]
+
+
+@pytest.mark.parametrize("bits,algo", ALGO_BITS)
+def test_every_kept_shape_gives_the_oracles_distances(mt, bits, algo):
+    """mt_eda_set_shape: every valid shape (lanes per pair, refilled lanes, pairs per steal from
+    1 to 4096, CTAs of 1 to 32 warps), each class of one call on a different shape (so a call
+    mixes refilled and lockstep launches and widened groups), gives the oracle's distances;
+    mt_eda_shape_for reports what was kept and lanes_per_pair = 0 brings the default back."""
+    pairs = _all_class_pairs(40 + algo)
+    dev = to_dev(pairs, mt)
+    ref = oracle.eda_batch(pairs, threads=8, algo=algo)
+    shapes = _shapes(bits)
+    try:
+        for i in range(len(shapes)):
+            for c, e in enumerate(CLASS_E):
+                mt.eda_set_shape(bits, False, e, *shapes[(i + c) % len(shapes)])
+            got = mt.eda_shape_for(bits, False, CLASS_E[0])
+            G, ch, cta, rf = shapes[i]
+            assert got == {"lanes_per_pair": G, "pairs_per_chunk": ch, "cta_threads": cta, "refill": rf, "tuned": 1}
+            dist = mt.eda_batch(*dev, mode=bits).cpu().numpy()
+            bad = np.flatnonzero(dist != ref)
+            assert len(bad) == 0, (shapes[i], bad[:5], dist[bad[:5]], ref[bad[:5]])
+    finally:
+        for e in CLASS_E:
+            mt.eda_set_shape(bits, False, e, 0)
+    assert all(mt.eda_shape_for(bits, False, e)["tuned"] == 0 for e in CLASS_E)
+    assert np.array_equal(mt.eda_batch(*dev, mode=bits).cpu().numpy(), ref)
+
+
+def test_classification_on_kept_shapes(mt):
+    """A classification runs the shape kept for its class (refilled lanes, one-pair steals on
+    one-warp CTAs, whole-warp groups) and its outputs equal the oracle's on every one."""
+    from helpers import compare_classify, oracle_params
+    c = gen.config(2, n_genomes=20, genome_len=100_000, n_reads=20_000)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    prm = dict(e_abs=12, e_permille=0, min_seeds=3, top_n=3, max_occ=1024)
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=8)
+    try:
+        for shape in ((1, 64, 256, 1), (1, 1, 32, 0), (4, 4096, 1024, 0), (32, 7, 96, 0)):
+            mt.eda_set_shape(0, True, 12, *shape)
+            compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
+    finally:
+        mt.eda_set_shape(0, True, 12, 0)
+        ix.close()
+    assert mt.eda_shape_for(0, True, 12)["tuned"] == 0
