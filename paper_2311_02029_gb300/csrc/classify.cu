@@ -68,8 +68,11 @@ struct WarpSmem {
         } t;
         struct {
             uint16_t gs[HCAP + 1];  // starts of (genome, strand) groups in the sorted matches
-            HitT qk[HCAP];          // qualifying locations: key of the first match
-            uint16_t qn[HCAP];      //                       seed count
+            // qualifying locations: 32-bit match keys as one rank word each,
+            // (0xFFFF - seed count) << 32 | key of the first match; 64-bit keys as key and count
+            uint64_t qr[sizeof(HitT) == 4 ? HCAP : 1];
+            HitT qk[sizeof(HitT) == 4 ? 1 : HCAP];
+            uint16_t qn[sizeof(HitT) == 4 ? 1 : HCAP];
             uint32_t qcount;
         } wk;
     } u;
@@ -170,7 +173,7 @@ MT_DEV bool warp_pack(const uint8_t *reads, uint64_t n_bases, int vec_ok, uint64
             } else {
                 x0 = x1 = 0;
                 const uint64_t p0 = start + j, end = start + n;
-#pragma unroll
+#pragma unroll 1
                 for (int q = 0; q < 8; q++) {
                     const uint32_t by = (p0 + q < end) ? reads[p0 + q] : 'A';
                     if (q < 4) x0 |= by << (8 * q); else x1 |= by << (8 * (q - 4));
@@ -280,40 +283,56 @@ template <> struct HitKey<false> {
     MT_DEV uint64_t wide(T h) const { return h; }
 };
 
-// Bitonic sort of 32*R keys held in registers, ascending: element r*32 + lane in v[r].
-// Exchanges across lanes use shuffles, exchanges across register slots stay in the lane.
+// One merge stage of a bitonic sort in registers (element r*32 + lane in v[r]), in its
+// mirrored form: blocks of k keys whose halves are each ascending become ascending. Key i is
+// first compared with its mirror i ^ (k - 1) in the block, then with i ^ j for j = k/4 .. 1;
+// every compare keeps the smaller key at the lower index, so its direction depends only on the
+// lane bit (or register slot) it exchanges across. Exchanges across lanes are shuffles.
 template <int R, typename T>
-MT_DEV void bitonic_regs(T (&v)[R]) {
+MT_DEV void bitonic_stage(T (&v)[R], uint32_t k) {
     const uint32_t lane = lane_id();
-    constexpr uint32_t P = 32u * R;
+    if (k <= 32) {
 #pragma unroll
-    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (int r = 0; r < R; r++) {
+            const T o = __shfl_xor_sync(FULL, v[r], k - 1);
+            v[r] = (lane & (k >> 1)) == 0 ? min(v[r], o) : max(v[r], o);
+        }
+    } else {
+        const int rm = (int)(k >> 5) - 1;          // mirrored register slots: r ^ rm, lane ^ 31
 #pragma unroll
-        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-            if (j >= 32) {
-#pragma unroll
-                for (int r = 0; r < R; r++) {
-                    const int pr = r ^ (int)(j >> 5);
-                    if (pr > r) {
-                        const uint32_t i = (uint32_t)r * 32u + lane;
-                        const bool up = (i & k) == 0;
-                        const T a = v[r], b = v[pr];
-                        v[r] = up ? min(a, b) : max(a, b);
-                        v[pr] = up ? max(a, b) : min(a, b);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; r++) {
-                    const uint32_t i = (uint32_t)r * 32u + lane;
-                    const T o = __shfl_xor_sync(FULL, v[r], j);
-                    // keep the smaller key where this lane's bit j agrees with the block's direction
-                    const bool keep_min = ((i & k) == 0) == ((lane & j) == 0);
-                    v[r] = keep_min ? min(v[r], o) : max(v[r], o);
-                }
+        for (int r = 0; r < R; r++) {
+            const int pr = r ^ rm;
+            if (pr > r) {
+                const T a = v[r], b = v[pr];
+                const T ob = __shfl_xor_sync(FULL, b, 31), oa = __shfl_xor_sync(FULL, a, 31);
+                v[r] = min(a, ob);
+                v[pr] = max(b, oa);
             }
         }
     }
+#pragma unroll
+    for (uint32_t j = k >> 2; j > 0; j >>= 1) {
+        if (j >= 32) {
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int pr = r ^ (int)(j >> 5);
+                if (pr > r) { const T a = v[r], b = v[pr]; v[r] = min(a, b); v[pr] = max(a, b); }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const T o = __shfl_xor_sync(FULL, v[r], j);
+                v[r] = (lane & j) == 0 ? min(v[r], o) : max(v[r], o);
+            }
+        }
+    }
+}
+
+// Bitonic sort of 32*R keys held in registers, ascending: element r*32 + lane in v[r].
+template <int R, typename T>
+MT_DEV void bitonic_regs(T (&v)[R]) {
+#pragma unroll
+    for (uint32_t k = 2; k <= 32u * R; k <<= 1) bitonic_stage<R, T>(v, k);
 }
 
 template <int R, typename T>
@@ -330,6 +349,42 @@ MT_DEV void sort_regs(T *h, uint32_t H) {
     for (int r = 0; r < R; r++) {
         const uint32_t i = (uint32_t)r * 32u + lane;
         if (i < H) h[i] = v[r];
+    }
+    __syncwarp();
+}
+
+// 33..128 keys: each 64-key half sorted in registers by one copy of the 64-key network, then
+// one merge stage over all 128.
+template <typename T>
+MT_DEV void sort_regs128(T *h, uint32_t H) {
+    const uint32_t lane = lane_id();
+    const uint32_t halves = H > 64 ? 2u : 1u;
+#pragma unroll 1
+    for (uint32_t q = 0; q < halves; q++) {
+        T v[2];
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const uint32_t i = 64u * q + (uint32_t)r * 32u + lane;
+            v[r] = i < H ? h[i] : (T)~(T)0;
+        }
+        bitonic_regs<2, T>(v);
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const uint32_t i = 64u * q + (uint32_t)r * 32u + lane;
+            if (i < H || halves == 2) h[i] = v[r];
+        }
+    }
+    if (halves == 2) {
+        __syncwarp();
+        T v[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) v[r] = h[(uint32_t)r * 32u + lane];
+        bitonic_stage<4, T>(v, 128);
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const uint32_t i = (uint32_t)r * 32u + lane;
+            if (i < H) h[i] = v[r];
+        }
     }
     __syncwarp();
 }
@@ -356,8 +411,7 @@ MT_DEV void warp_bitonic(T *a, uint32_t P) {
 template <typename T>
 MT_DEV void sort_hits(T *h, uint32_t H) {
     if (H <= 32) sort_regs<1, T>(h, H);
-    else if (H <= 64) sort_regs<2, T>(h, H);
-    else if (H <= 128) sort_regs<4, T>(h, H);
+    else if (H <= 128) sort_regs128<T>(h, H);
     else {
         uint32_t P = 128;
         while (P < H) P <<= 1;
@@ -450,6 +504,7 @@ MT_DEV uint32_t minimizers_w11(WS &ws, uint32_t t0, uint32_t tw, uint32_t k, uin
             const uint32_t j = b + a;
             uint32_t best = j;
             uint64_t bk = mix64(ws.u.t.code[j] & CODE_MASK62);
+#pragma unroll 1
             for (uint32_t t = j + 1; t < j + 11; t++) {
                 const uint64_t kk = mix64(ws.u.t.code[t] & CODE_MASK62);
                 if (kk < bk) { bk = kk; best = t; }
@@ -807,6 +862,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                     }
                     __syncwarp();
                     uint32_t before = 0;    // lookups starting before this pass
+#pragma unroll 1
                     for (uint32_t q0 = 0; q0 < total; q0 += 32) {
                         const uint32_t bit = (cnt && pre >= q0 && pre < q0 + 32) ? (1u << (pre - q0)) : 0u;
                         const uint32_t M = __reduce_or_sync(FULL, bit);
@@ -822,7 +878,7 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                     }
                 } else {
                     if (ni && cnt) {
-#pragma unroll
+#pragma unroll 1
                         for (uint32_t t = 0; t < 3; t++)
                             if (t < cnt) add_hits<SMEM_HIST, true>(hist, A.ghits, (uint32_t)((t == 0 ? w1 : (t == 1 ? w2 : w3)) >> 33), 1u);
                     }
@@ -876,8 +932,12 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                 const uint32_t e = lower_bound_t<HitT>(ws.hits, s + 1, ge, (HitT)(ws.hits[s] + E + 1));
                 if (e - s >= A.min_seeds) {
                     const uint32_t qi = atomicAdd(&ws.u.wk.qcount, 1u);
-                    ws.u.wk.qk[qi] = ws.hits[s];
-                    ws.u.wk.qn[qi] = (uint16_t)(e - s);
+                    if constexpr (HK32) {
+                        ws.u.wk.qr[qi] = ((uint64_t)(0xFFFFu - (e - s)) << 32) | ws.hits[s];
+                    } else {
+                        ws.u.wk.qk[qi] = ws.hits[s];
+                        ws.u.wk.qn[qi] = (uint16_t)(e - s);
+                    }
                 }
                 s = e;
             }
@@ -886,13 +946,21 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
         const uint32_t Q = ws.u.wk.qcount;
         // rank the qualifying locations: seeds descending, then (genome, strand, diagonal)
         for (uint32_t qi = lane; qi < Q; qi += 32) {
-            const uint32_t seeds_i = ws.u.wk.qn[qi];
-            const HitT hk_i = ws.u.wk.qk[qi];
-            uint32_t rank = 0;
-            for (uint32_t qj = 0; qj < Q; qj++) {
-                const uint32_t seeds_j = ws.u.wk.qn[qj];
-                const HitT hk_j = ws.u.wk.qk[qj];
-                rank += (seeds_j > seeds_i) || (seeds_j == seeds_i && hk_j < hk_i);
+            uint32_t seeds_i, rank = 0;
+            HitT hk_i;
+            if constexpr (HK32) {   // one compare of rank words (they are distinct)
+                const uint64_t ri = ws.u.wk.qr[qi];
+                for (uint32_t qj = 0; qj < Q; qj++) rank += ws.u.wk.qr[qj] < ri;
+                seeds_i = 0xFFFFu - (uint32_t)(ri >> 32);
+                hk_i = (HitT)ri;
+            } else {
+                seeds_i = ws.u.wk.qn[qi];
+                hk_i = ws.u.wk.qk[qi];
+                for (uint32_t qj = 0; qj < Q; qj++) {
+                    const uint32_t seeds_j = ws.u.wk.qn[qj];
+                    const HitT hk_j = ws.u.wk.qk[qj];
+                    rank += (seeds_j > seeds_i) || (seeds_j == seeds_i && hk_j < hk_i);
+                }
             }
             if (rank < CSTORE) {
                 Cluster c;
