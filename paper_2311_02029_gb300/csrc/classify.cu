@@ -353,8 +353,37 @@ MT_DEV void sort_regs(T *h, uint32_t H) {
     __syncwarp();
 }
 
+// Mirrored bitonic sort of 64 keys in registers with key 2*lane + r in v[r], so that the
+// compares at distance 1 stay in the lane and the others exchange with lane ^ (distance / 2).
+template <typename T>
+MT_DEV void bitonic_pairs64(T (&v)[2]) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (uint32_t k = 2; k <= 64; k <<= 1) {
+        if (k > 2) {   // mirror: key i with i ^ (k - 1), i.e. slot r ^ 1 of lane ^ ((k - 1) / 2)
+            const uint32_t m = (k - 1) >> 1;
+            const bool lo = (lane & (k >> 2)) == 0;
+            const T o0 = __shfl_xor_sync(FULL, v[1], m), o1 = __shfl_xor_sync(FULL, v[0], m);
+            v[0] = lo ? min(v[0], o0) : max(v[0], o0);
+            v[1] = lo ? min(v[1], o1) : max(v[1], o1);
+        }
+#pragma unroll
+        for (uint32_t j = (k == 2 ? 1u : k >> 2); j > 1; j >>= 1) {
+            const bool lo = (lane & (j >> 1)) == 0;
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const T o = __shfl_xor_sync(FULL, v[r], j >> 1);
+                v[r] = lo ? min(v[r], o) : max(v[r], o);
+            }
+        }
+        const T a = v[0], b = v[1];   // distance 1 (and the mirror of k = 2)
+        v[0] = min(a, b);
+        v[1] = max(a, b);
+    }
+}
+
 // 33..128 keys: each 64-key half sorted in registers by one copy of the 64-key network, then
-// one merge stage over all 128.
+// one mirrored merge stage over all 128 (key 64q + 2*lane + r in v[2q + r]).
 template <typename T>
 MT_DEV void sort_regs128(T *h, uint32_t H) {
     const uint32_t lane = lane_id();
@@ -364,13 +393,13 @@ MT_DEV void sort_regs128(T *h, uint32_t H) {
         T v[2];
 #pragma unroll
         for (int r = 0; r < 2; r++) {
-            const uint32_t i = 64u * q + (uint32_t)r * 32u + lane;
+            const uint32_t i = 64u * q + 2u * lane + (uint32_t)r;
             v[r] = i < H ? h[i] : (T)~(T)0;
         }
-        bitonic_regs<2, T>(v);
+        bitonic_pairs64<T>(v);
 #pragma unroll
         for (int r = 0; r < 2; r++) {
-            const uint32_t i = 64u * q + (uint32_t)r * 32u + lane;
+            const uint32_t i = 64u * q + 2u * lane + (uint32_t)r;
             if (i < H || halves == 2) h[i] = v[r];
         }
     }
@@ -378,11 +407,29 @@ MT_DEV void sort_regs128(T *h, uint32_t H) {
         __syncwarp();
         T v[4];
 #pragma unroll
-        for (int r = 0; r < 4; r++) v[r] = h[(uint32_t)r * 32u + lane];
-        bitonic_stage<4, T>(v, 128);
+        for (int r = 0; r < 4; r++) v[r] = h[64u * (r >> 1) + 2u * lane + (uint32_t)(r & 1)];
+        {   // mirror: key i of the first half with 127 - i (slot 3 - r of lane ^ 31)
+            const T o3 = __shfl_xor_sync(FULL, v[3], 31), o2 = __shfl_xor_sync(FULL, v[2], 31);
+            const T o1 = __shfl_xor_sync(FULL, v[1], 31), o0 = __shfl_xor_sync(FULL, v[0], 31);
+            v[0] = min(v[0], o3);
+            v[1] = min(v[1], o2);
+            v[2] = max(v[2], o1);
+            v[3] = max(v[3], o0);
+        }
+#pragma unroll
+        for (uint32_t j = 32; j > 1; j >>= 1) {
+            const bool lo = (lane & (j >> 1)) == 0;
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const T o = __shfl_xor_sync(FULL, v[r], j >> 1);
+                v[r] = lo ? min(v[r], o) : max(v[r], o);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r += 2) { const T a = v[r], b = v[r + 1]; v[r] = min(a, b); v[r + 1] = max(a, b); }
 #pragma unroll
         for (int r = 0; r < 4; r++) {
-            const uint32_t i = (uint32_t)r * 32u + lane;
+            const uint32_t i = 64u * (r >> 1) + 2u * lane + (uint32_t)(r & 1);
             if (i < H) h[i] = v[r];
         }
     }
@@ -928,8 +975,11 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             uint32_t s = ws.u.wk.gs[gi];
             const uint32_t ge = ws.u.wk.gs[gi + 1];
             add_hits<SMEM_HIST, false>(hist, A.ghits, hf.genome(ws.hits[s]), ge - s);
+            const HitT last = ws.hits[ge - 1];
             while (s < ge) {
-                const uint32_t e = lower_bound_t<HitT>(ws.hits, s + 1, ge, (HitT)(ws.hits[s] + E + 1));
+                const HitT lim = (HitT)(ws.hits[s] + E + 1);
+                // most groups hold one location: the group's last match is already below lim
+                const uint32_t e = last < lim ? ge : lower_bound_t<HitT>(ws.hits, s + 1, ge, lim);
                 if (e - s >= A.min_seeds) {
                     const uint32_t qi = atomicAdd(&ws.u.wk.qcount, 1u);
                     if constexpr (HK32) {
