@@ -191,25 +191,7 @@ MT_DEV void do_items(const Src &src, const uint32_t *perm, uint64_t b, uint64_t 
 // case of sneaky_walk, no window bases outside the genome): from column c, the furthest
 // column any diagonal's zero run reaches.
 MT_DEV uint32_t snake_step(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t ndiag, uint32_t c) {
-    uint32_t best = c;
-    const uint64_t r0 = get32(rd, c);
-    for (uint32_t tb = 0; tb < ndiag; tb += 32) {   // blocks of 32 diagonals
-        const uint32_t q = c + tb;
-        const uint64_t w0 = get32(wn, q);
-        const uint64_t w1 = get32(wn, q + 32);
-        const uint32_t tn = min(32u, ndiag - tb);
-        for (uint32_t t = 0; t < tn; t++) {
-            const uint32_t sh = 2 * t;
-            const uint64_t x = t ? ((w0 >> sh) | (w1 << (64 - sh))) : w0;
-            const uint64_t y = r0 ^ x;
-            const uint64_t m = (y | (y >> 1)) & EVEN_BITS;
-            uint32_t e = m ? c + ((uint32_t)(__ffsll((long long)m) - 1) >> 1)
-                           : next_mismatch<false>(rd, wn, n, c + 32, tb + t, 0, 0);
-            e = e < n ? e : n;
-            best = e > best ? e : best;
-        }
-    }
-    return best;
+    return snake_diagonals<false>(rd, wn, n, c, 0, ndiag, 0, 0, c);
 }
 
 // SneakySnake with one lane per pair, each lane refilled on its own: every pass of the loop,
@@ -518,7 +500,11 @@ static uint32_t default_G(uint32_t E) {
     return G;
 }
 
+// The shape of a class never tuned: SneakySnake one lane per pair in 32-pair steals and
+// 512-thread CTAs (the shape the search keeps for the workloads measured), the other
+// approximations about three diagonals a lane.
 static TunedShape default_shape(int algo, uint32_t E) {
+    if (algo == ALGO_SNAKE) return TunedShape{1u, 32u, 512u, 0u};
     return TunedShape{algo == ALGO_QGRAM ? 32u : default_G(E), EDA_CHUNK, (uint32_t)EDA_THREADS, 0u};
 }
 

@@ -95,11 +95,65 @@ MT_DEV uint32_t sneaky_walk_cached(const uint64_t *rd, const uint64_t *wn, uint3
     return cnt < E + 1 ? cnt : E + 1;
 }
 
+// First mismatch at or after column c of the diagonals tb .. tb + tn - 1 (tn <= 17), the
+// furthest of them and `best`. The read's columns c .. c + 15 are r16 (2 bits a base); one
+// 64-bit window word (bases c + tb ..) holds columns c .. c + 15 of all tn diagonals, so each
+// diagonal costs a shift, an XOR, a fold and a find-first-set on 32 bits. A diagonal whose 16
+// columns all match (nearly only the location's own) walks on with next_mismatch. FULL: tn is
+// 17, and the pass is unrolled (constant shifts; the walks-on come after it).
+template <bool EDGES, bool FULL>
+MT_DEV uint32_t snake_block16(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t c, uint32_t r16,
+                              uint32_t tb, uint32_t tn, int32_t lo, int32_t hi, uint32_t best) {
+    const uint32_t q = c + tb;
+    const uint64_t w = get32(wn, q);
+    const uint64_t em = EDGES ? edge_mask((int32_t)q, lo, hi) : 0ull;
+    if (FULL) {
+        uint32_t open = 0;
+#pragma unroll
+        for (uint32_t t = 0; t < 17; t++) {
+            const uint32_t y = r16 ^ (uint32_t)(w >> (2 * t));
+            uint32_t m = (y | (y >> 1)) & 0x55555555u;
+            if (EDGES) m |= (uint32_t)(em >> (2 * t)) & 0x55555555u;
+            const uint32_t e = m ? min(c + ((uint32_t)(__ffs((int)m) - 1) >> 1), n) : c;
+            open |= (uint32_t)(m == 0) << t;
+            best = e > best ? e : best;
+        }
+        while (open) {
+            const uint32_t t = __ffs((int)open) - 1;
+            open &= open - 1;
+            const uint32_t e = min(next_mismatch<EDGES>(rd, wn, n, c + 16, tb + t, lo, hi), n);
+            best = e > best ? e : best;
+        }
+    } else {
+        for (uint32_t t = 0; t < tn; t++) {
+            const uint32_t y = r16 ^ (uint32_t)(w >> (2 * t));
+            uint32_t m = (y | (y >> 1)) & 0x55555555u;
+            if (EDGES) m |= (uint32_t)(em >> (2 * t)) & 0x55555555u;
+            uint32_t e;
+            if (m) e = c + ((uint32_t)(__ffs((int)m) - 1) >> 1);
+            else e = next_mismatch<EDGES>(rd, wn, n, c + 16, tb + t, lo, hi);
+            e = e < n ? e : n;
+            best = e > best ? e : best;
+        }
+    }
+    return best;
+}
+
+// Furthest first mismatch at or after column c over the diagonals [d0, d1) and `best`.
+template <bool EDGES>
+MT_DEV uint32_t snake_diagonals(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t c, uint32_t d0,
+                                uint32_t d1, int32_t lo, int32_t hi, uint32_t best) {
+    const uint32_t r16 = (uint32_t)get32(rd, c);
+    uint32_t tb = d0;
+    for (; tb + 17 <= d1; tb += 17) best = snake_block16<EDGES, true>(rd, wn, n, c, r16, tb, 17, lo, hi, best);
+    if (tb < d1) best = snake_block16<EDGES, false>(rd, wn, n, c, r16, tb, d1 - tb, lo, hi, best);
+    return best;
+}
+
 // The walk for one pair, executed by the G lanes of `gmask` (glane = lane within group).
 // Lane glane owns the contiguous diagonal range [glane*T, glane*T + T), T = ceil((2E+1)/G).
-// Per step it loads the read's 32 columns from c once and the window's bases from c + its
-// first diagonal (up to 32 + T bases) once; each diagonal's 32 columns then come from a
-// register funnel shift. Only a diagonal whose first 32 columns all match walks on further.
+// Per step it loads the read's 16 columns from c once and, per block of 17 diagonals, one
+// window word (snake_diagonals).
 template <int G, bool EDGES>
 MT_DEV uint32_t sneaky_walk(const uint64_t *rd, const uint64_t *wn, uint32_t n, uint32_t E,
                             int32_t lo, int32_t hi, unsigned gmask, uint32_t glane) {
@@ -110,27 +164,7 @@ MT_DEV uint32_t sneaky_walk(const uint64_t *rd, const uint64_t *wn, uint32_t n, 
     uint32_t c = 0, cnt = 0;
     while (c < n) {
         uint32_t best = c;
-        if (d0 < d1) {
-            const uint64_t r0 = get32(rd, c);
-            for (uint32_t tb = d0; tb < d1; tb += 32) {   // blocks of 32 diagonals
-                const uint32_t q = c + tb;
-                const uint64_t w0 = get32(wn, q);
-                const uint64_t w1 = get32(wn, q + 32);
-                const uint32_t tn = min(32u, d1 - tb);
-                for (uint32_t t = 0; t < tn; t++) {
-                    const uint32_t sh = 2 * t;
-                    const uint64_t x = t ? ((w0 >> sh) | (w1 << (64 - sh))) : w0;
-                    const uint64_t y = r0 ^ x;
-                    uint64_t m = (y | (y >> 1)) & EVEN_BITS;
-                    if (EDGES) m |= edge_mask((int32_t)(q + t), lo, hi);
-                    uint32_t e;
-                    if (m) e = c + ((uint32_t)(__ffsll((long long)m) - 1) >> 1);
-                    else e = next_mismatch<EDGES>(rd, wn, n, c + 32, tb + t, lo, hi);
-                    e = e < n ? e : n;
-                    best = e > best ? e : best;
-                }
-            }
-        }
+        if (d0 < d1) best = snake_diagonals<EDGES>(rd, wn, n, c, d0, d1, lo, hi, best);
         if (G > 1) best = __reduce_max_sync(gmask, best);
         c = best;
         if (c >= n) break;
