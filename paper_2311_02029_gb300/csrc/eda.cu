@@ -53,8 +53,10 @@ struct BatchSrc {
         const uint64_t *rs = rw + (r0 >> 5) + r;
         const uint64_t *ws = ww + (woff[p] >> 5) + p;
         uint32_t nr = (n + 31) / 32, nwn = (n + 2 * E_ + 31) / 32;
-        for (uint32_t t = gl; t < nr + 2; t += G) rd[t] = t < nr ? rs[t] : 0ull;
-        for (uint32_t t = gl; t < nwn + 3; t += G) wn[t] = t < nwn ? ws[t] : 0ull;
+#pragma unroll 4
+        for (uint32_t t = gl; t < nr + 2; t += G) rd[t] = t < nr ? __ldg(rs + t) : 0ull;
+#pragma unroll 4
+        for (uint32_t t = gl; t < nwn + 3; t += G) wn[t] = t < nwn ? __ldg(ws + t) : 0ull;
         PairInfo pi;
         pi.n = n; pi.E = E_; pi.lo = 0; pi.hi = (int32_t)(n + 2 * E_); pi.edges = false;
         return pi;
@@ -64,11 +66,20 @@ struct BatchSrc {
 
 // 32 bases of a genome starting at `pos` (may lie outside the genome; those bits are
 // don't-care and are masked as obstacles by the caller). Reads only words 0..nwg of it.
+// Staging loads go through the read-only path, so that a staging loop's loads (the staged
+// words are stored to shared memory between them) can all be in flight together.
 MT_DEV uint64_t genome_get32(const uint64_t *g, uint64_t nwg, int64_t pos) {
     int64_t wi = pos >> 5;
     uint32_t sh = (uint32_t)(pos & 31) * 2u;
-    uint64_t a = (wi >= 0 && wi <= (int64_t)nwg) ? g[wi] : 0ull;
-    uint64_t b = (wi + 1 >= 0 && wi + 1 <= (int64_t)nwg) ? g[wi + 1] : 0ull;
+    uint64_t a = (wi >= 0 && wi <= (int64_t)nwg) ? __ldg(g + wi) : 0ull;
+    uint64_t b = (wi + 1 >= 0 && wi + 1 <= (int64_t)nwg) ? __ldg(g + wi + 1) : 0ull;
+    return (a >> sh) | ((b << 1) << (63u - sh));
+}
+
+// get32 of a packed sequence in global memory, through the read-only path.
+MT_DEV uint64_t ldg_get32(const uint64_t *s, uint32_t pos) {
+    const uint32_t wi = pos >> 5, sh = (pos & 31u) * 2u;
+    const uint64_t a = __ldg(s + wi), b = __ldg(s + wi + 1);
     return (a >> sh) | ((b << 1) << (63u - sh));
 }
 
@@ -96,17 +107,19 @@ struct ClassifySrc {
         const uint64_t *rs = rw + seq_word(ro, io->off0, r);
         uint32_t nr = (n + 31) / 32;
         if (hk_rel(c.hkey)) {
+#pragma unroll 4
             for (uint32_t t = gl; t < nr + 2; t += G) {
                 uint64_t x = 0;
                 if (t < nr) {
                     int32_t st = (int32_t)n - 32 * (int32_t)(t + 1);
-                    x = st >= 0 ? get32(rs, (uint32_t)st) : (get32(rs, 0) << (2 * (uint32_t)(-st)));
+                    x = st >= 0 ? ldg_get32(rs, (uint32_t)st) : (ldg_get32(rs, 0) << (2 * (uint32_t)(-st)));
                     x = ~rev2(x);
                 }
                 rd[t] = x;
             }
         } else {
-            for (uint32_t t = gl; t < nr + 2; t += G) rd[t] = t < nr ? rs[t] : 0ull;
+#pragma unroll 4
+            for (uint32_t t = gl; t < nr + 2; t += G) rd[t] = t < nr ? __ldg(rs + t) : 0ull;
         }
         uint32_t g = hk_genome(c.hkey);
         int64_t wstart = hk_diag(c.hkey) - (int64_t)E;
@@ -114,6 +127,7 @@ struct ClassifySrc {
         uint64_t nwg = (glen + 31) / 32;
         const uint64_t *gp = ix.ref + ix.gword[g];
         uint32_t L = n + 2 * E, nwn = (L + 31) / 32;
+#pragma unroll 4
         for (uint32_t t = gl; t < nwn + 3; t += G)
             wn[t] = t < nwn ? genome_get32(gp, nwg, wstart + 32 * (int64_t)t) : 0ull;
         int64_t lo = -wstart, hi = (int64_t)glen - wstart;
@@ -416,8 +430,12 @@ struct EdaShape {
     uint32_t rww, www, xw;
 };
 
+// The words a group takes are odd in number, so that the groups of a warp (one lane each
+// when G = 1) reach their 8-byte words in different shared-memory banks.
 static EdaShape eda_shape(int A, uint32_t maxn, uint32_t maxE) {
-    return EdaShape{eda_read_words(maxn), eda_win_words(maxn, maxE), eda_extra_words(A, maxn)};
+    EdaShape w{eda_read_words(maxn), eda_win_words(maxn, maxE), eda_extra_words(A, maxn)};
+    if ((w.rww + w.www + w.xw) % 2 == 0) w.www++;
+    return w;
 }
 
 static constexpr size_t EDA_SMEM_MAX = 200 * 1024;
