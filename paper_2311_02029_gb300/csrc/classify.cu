@@ -54,6 +54,7 @@ static constexpr int FB_THREADS = 256;
 // per-position keys (W11: key[] shrinks to one word).
 template <typename HitT, bool W11 = false>
 struct WarpSmem {
+    unsigned long long stat[4];     // the warp's minimizers, matches, list occurrences, stored locations
     uint64_t rd[RDW];               // packed read
     HitT hits[HCAP];                // seed-match keys of the read
     union {                         // the tiles of a read, then its location walk
@@ -616,10 +617,19 @@ static size_t seed_smem_bytes(uint32_t hist_n) {
     return (((size_t)hist_n * 4 + 15) & ~(size_t)15) + SEED_WARPS * sizeof(WarpSmem<HitT, W11>);
 }
 
+// Resident CTAs per SM of a seeding kernel. The mapping kernel of the w = 11 path with 32-bit
+// match keys fits five in shared memory, and 48 registers a thread; it then keeps its
+// statistics and the batch description in shared memory, not in registers.
+template <bool HK32, bool COUNT, bool W11>
+struct SeedLean {
+    static constexpr bool value = HK32 && W11 && !COUNT;
+    static constexpr int ctas = value ? 5 : 4;
+};
+
 // W11: the index has w = 11 and k <= 28, and the minimizers come from the block path
 // (minimizers_w11); otherwise the general window-minimum path runs.
 template <bool SMEM_HIST, bool HK32, bool COUNT = false, bool HPC = false, bool MULTI = false, bool W11 = false>
-__global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
+__global__ void __launch_bounds__(SEED_THREADS, (SeedLean<HK32, COUNT, W11>::ctas)) k_seed(SeedArgs A) {
     static_assert(!MULTI || (COUNT && !HK32), "several indexes are only counted");
     static_assert(!(MULTI && W11), "the block path keeps no keys for several tables");
     using HitT = typename HitKey<HK32>::T;
@@ -637,9 +647,19 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
     const uint32_t k = A.ix.k, w = A.ix.w, canonical = A.ix.canonical;
     HitKey<HK32> hf;
     hf.db = A.ix.hk_db;
-    unsigned long long n_mins = 0, n_hits = 0, n_ext = 0, n_stored = 0;
-
-    const IoBlock io = *A.io;
+    // statistics: minimizers, matches, list occurrences, stored locations (warp-uniform)
+    constexpr bool LEAN = SeedLean<HK32, COUNT, W11>::value;
+    unsigned long long st_mins = 0, st_hits = 0, st_ext = 0, st_stored = 0;
+    if (LEAN && lane < 4) ws.stat[lane] = 0;
+    __shared__ IoBlock s_io;
+    IoBlock io_r;
+    if (LEAN) {
+        if (threadIdx.x == 0) s_io = *A.io;
+        __syncthreads();
+    } else {
+        io_r = *A.io;
+    }
+    const IoBlock &io = LEAN ? s_io : io_r;
     const uint64_t total_warps = (uint64_t)gridDim.x * SEED_WARPS;
     const uint64_t r_end = umin64(A.r_end, io.n_reads);
     for (uint64_t r = A.r_begin + (uint64_t)blockIdx.x * SEED_WARPS + warp; r < r_end; r += total_warps) {
@@ -765,7 +785,8 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             }
             }
             __syncwarp();
-            n_mins += nm;
+            if (!LEAN) st_mins += nm;
+            else if (lane == 0) ws.stat[0] += nm;
             if (MULTI) {
                 // (minimizer, batch) pairs: the batches' key filters (small, in L2) are tested
                 // MULTI_UNROLL pairs a lane at a time (their loads in flight together); the pairs that pass
@@ -826,11 +847,15 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                                 s = (s + 1) & bv.slot_mask;
                             }
                             if (cnt > A.max_occ) cnt = 0;
-                            if (!ni) n_ext += cnt;
                             base = bv.base;
                             occ = bv.occ;
                         }
                         H += __shfl_sync(FULL, warp_incl_scan(cnt), 31);
+                        {
+                            const uint32_t ext = __reduce_add_sync(FULL, ni ? 0u : cnt);
+                            if (!LEAN) st_ext += ext;
+                            else if (lane == 0) ws.stat[2] += ext;
+                        }
                         if (ni && cnt) {
 #pragma unroll
                             for (uint32_t t = 0; t < 3; t++)
@@ -886,7 +911,11 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                         s = (s + 1) & A.ix.slot_mask;
                     }
                     if (cnt > A.max_occ) cnt = 0;
-                    if (!ni) n_ext += cnt;
+                }
+                {
+                    const uint32_t ext = __reduce_add_sync(FULL, ni ? 0u : cnt);
+                    if (!LEAN) st_ext += ext;
+                    else if (lane == 0) ws.stat[2] += ext;
                 }
                 const uint32_t incl = warp_incl_scan(cnt);
                 const uint32_t total = __shfl_sync(FULL, incl, 31);
@@ -943,7 +972,8 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
             }
             __syncwarp();
         }
-        n_hits += H;
+        if (!LEAN) st_hits += H;
+        else if (lane == 0) ws.stat[1] += H;
         if (COUNT) continue;
         if (ovf) {
             if (lane == 0) {
@@ -1018,15 +1048,19 @@ __global__ void __launch_bounds__(SEED_THREADS, 4) k_seed(SeedArgs A) {
                 A.clus[r * CSTORE + rank] = c;
             }
         }
-        if (lane == 0) { A.qcnt[r] = Q; n_stored += min(Q, CSTORE); }
+        if (lane == 0) {
+            A.qcnt[r] = Q;
+            if (!LEAN) st_stored += min(Q, CSTORE);
+            else ws.stat[3] += min(Q, CSTORE);
+        }
         __syncwarp();
     }
-    for (int o = 16; o > 0; o >>= 1) n_ext += __shfl_xor_sync(FULL, n_ext, o);
+    __syncwarp();
     if (lane == 0) {
-        atomicAdd(&A.ctr->stat[ST_MINS], n_mins);
-        atomicAdd(&A.ctr->stat[ST_HITS], n_hits);
-        atomicAdd(&A.ctr->stat[ST_EXT], n_ext);
-        atomicAdd(&A.ctr->stat[ST_STORED], n_stored);
+        atomicAdd(&A.ctr->stat[ST_MINS], LEAN ? ws.stat[0] : st_mins);
+        atomicAdd(&A.ctr->stat[ST_HITS], LEAN ? ws.stat[1] : st_hits);
+        atomicAdd(&A.ctr->stat[ST_EXT], LEAN ? ws.stat[2] : st_ext);
+        atomicAdd(&A.ctr->stat[ST_STORED], LEAN ? ws.stat[3] : st_stored);
     }
     if (SMEM_HIST) {
         __syncthreads();
