@@ -1101,9 +1101,11 @@ __global__ void k_mask(const unsigned long long *hits, uint32_t G, uint32_t num,
 // usually a divergent genome walked to E + 1 obstacles, so a warp of the approximation kernel
 // that takes consecutive candidates walks them for similar numbers of steps. The order of the
 // list changes no result (each distance goes to its candidate's slot).
-__global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep,
-                         uint32_t top_n, Cluster *cand, uint8_t *nloc_ws, uint32_t *cl, uint32_t *fb_list,
-                         Counters *ctr) {
+static constexpr int SELECT_CTAS = 6;   // resident k_select CTAs an SM (40 registers)
+
+__global__ void __launch_bounds__(256, SELECT_CTAS)
+k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uint8_t *keep, uint32_t top_n,
+         Cluster *cand, uint8_t *nloc_ws, uint32_t *cl, uint32_t *fb_list, Counters *ctr) {
     constexpr uint32_t BINS = 64;
     __shared__ uint32_t s_bin[BINS];
     __shared__ unsigned long long s_base;
@@ -1121,8 +1123,26 @@ __global__ void k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster 
                 fb = false;   // queued by the seeding pass
                 nloc_ws[r] = 0;
             } else {
-                uint32_t lim = min(q, CSTORE);
-                for (uint32_t i = 0; i < lim && taken < top_n; i++) {
+                const uint32_t lim = min(q, CSTORE);
+                // the first four locations and their genomes' verdicts are loaded together
+                Cluster c4[4];
+                bool k4[4];
+#pragma unroll
+                for (uint32_t i = 0; i < 4; i++) {
+                    c4[i].hkey = 0; c4[i].seeds = 0; c4[i].pad = 0;
+                    if (i < lim) c4[i] = clus[r * CSTORE + i];
+                }
+#pragma unroll
+                for (uint32_t i = 0; i < 4; i++) k4[i] = i < lim && keep[hk_genome(c4[i].hkey)];
+#pragma unroll
+                for (uint32_t i = 0; i < 4; i++) {
+                    if (k4[i] && taken < top_n) {
+                        const uint32_t bin = BINS - 1 - min(c4[i].seeds, BINS - 1);
+                        bins |= (uint64_t)bin << (6 * taken);
+                        cand[r * top_n + taken++] = c4[i];
+                    }
+                }
+                for (uint32_t i = 4; i < lim && taken < top_n; i++) {
                     Cluster c = clus[r * CSTORE + i];
                     if (keep[hk_genome(c.hkey)]) {
                         const uint32_t bin = BINS - 1 - min(c.seeds, BINS - 1);
@@ -1320,7 +1340,9 @@ struct DecideArgs {
 // from there, and the location records go out as contiguous 8-byte words.
 static constexpr int DECIDE_THREADS = 256;
 
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
+// TNMAX: the largest top_n of the launch (the per-read arrays below are sized by it).
+template <uint32_t TNMAX>
+__global__ void __launch_bounds__(DECIDE_THREADS, (TNMAX <= 3 ? 6 : 3)) k_decide(DecideArgs A) {
     extern __shared__ __align__(16) unsigned char dsm[];
     const uint32_t tn = A.top_n;
     // unique counts of the block (G counters), flushed once at the end
@@ -1352,12 +1374,12 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
             const uint32_t E = edit_threshold(n, A.e_abs, A.e_permille);
             const uint32_t nl = s_nloc[threadIdx.x];
             cand += nl;
-            // every loop below runs over the at most MT_MAX_TOPN slots with static indices
-            uint32_t d[MT_MAX_TOPN];
-            Cluster cl[MT_MAX_TOPN];
+            // every loop below runs over the at most TNMAX slots with static indices
+            uint32_t d[TNMAX];
+            Cluster cl[TNMAX];
             uint32_t best = E + 1;
 #pragma unroll
-            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+            for (uint32_t t = 0; t < TNMAX; t++) {
                 d[t] = 0xFFu;
                 cl[t].hkey = 0; cl[t].seeds = 0; cl[t].pad = 0;
                 if (t < nl) {
@@ -1367,10 +1389,10 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
                 }
             }
             int32_t tax = -1;
-            int32_t S[MT_MAX_TOPN];
+            int32_t S[TNMAX];
             uint32_t ns = 0;
 #pragma unroll
-            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+            for (uint32_t t = 0; t < TNMAX; t++) {
                 S[t] = -1;
                 if (t < nl && best <= E && d[t] == best) {
                     const int32_t g = (int32_t)hk_genome(cl[t].hkey);
@@ -1382,7 +1404,7 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
                 }
             }
 #pragma unroll
-            for (uint32_t t = 0; t < MT_MAX_TOPN; t++) {
+            for (uint32_t t = 0; t < TNMAX; t++) {
                 if (t < tn && io.locs) {
                     mt_loc L;
                     memset(&L, 0, sizeof(L));
@@ -1405,10 +1427,10 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(DecideArgs A) {
                 // the distinct genomes at the best distance, in rank order, then -1
                 uint32_t o = 0;
 #pragma unroll
-                for (uint32_t t = 0; t < MT_MAX_TOPN; t++)
+                for (uint32_t t = 0; t < TNMAX; t++)
                     if (S[t] >= 0) { A.multi_set[r * tn + o] = S[t]; o++; }
 #pragma unroll
-                for (uint32_t t = 0; t < MT_MAX_TOPN; t++)
+                for (uint32_t t = 0; t < TNMAX; t++)
                     if (t >= o && t < tn) A.multi_set[r * tn + t] = -1;
             }
             acc += (best <= E);
@@ -1838,7 +1860,7 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
             k_mask<<<1, 1024, 0, s>>>(ghits, G, p->cont_num, p->cont_den, (uint8_t *)P(L.keep));
             MT_CK(cudaGetLastError());
         }
-        const unsigned rblocks = (unsigned)std::min<uint64_t>((c.cap_reads + 255) / 256, (uint64_t)sm_count() * 8);
+        const unsigned rblocks = (unsigned)std::min<uint64_t>((c.cap_reads + 255) / 256, (uint64_t)sm_count() * SELECT_CTAS);
         k_select<<<rblocks, 256, 0, s>>>(io, A.qcnt, A.clus, (const uint8_t *)P(L.keep), top_n, (Cluster *)P(L.cand),
                                          (uint8_t *)P(L.nloc_ws), (uint32_t *)P(L.cl), A.fb_list, ctr);
         MT_CK(cudaGetLastError());
@@ -1882,11 +1904,16 @@ static int enqueue_classify(EnqueueCtx &c, cudaStream_t s) {
             D.hist = G <= SMEM_HIST_MAX;
             const size_t dsmem = (D.hist ? (((size_t)G * 8 + 15) & ~(size_t)15) : 0) +
                                  (size_t)DECIDE_THREADS * top_n * (sizeof(Cluster) + sizeof(mt_loc) + 1) + DECIDE_THREADS;
-            const unsigned dblocks = (unsigned)std::min<uint64_t>((c.cap_reads + DECIDE_THREADS - 1) / DECIDE_THREADS,
-                                                                  (uint64_t)sm_count() * 8);
+            // the paper's top 3 runs a variant with per-read arrays of 3 (fewer registers, more
+            // resident CTAs); one wave of resident CTAs walks the reads
+            auto kern = top_n <= 3 ? k_decide<3> : k_decide<MT_MAX_TOPN>;
             if (dsmem > 48 * 1024)
-                MT_CK(cudaFuncSetAttribute(k_decide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
-            k_decide<<<dblocks, DECIDE_THREADS, dsmem, s>>>(D);
+                MT_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+            int per_sm = 0;
+            MT_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, DECIDE_THREADS, dsmem));
+            const unsigned dblocks = (unsigned)std::min<uint64_t>((c.cap_reads + DECIDE_THREADS - 1) / DECIDE_THREADS,
+                                                                  (uint64_t)sm_count() * std::max(per_sm, 1));
+            kern<<<dblocks, DECIDE_THREADS, dsmem, s>>>(D);
         }
         MT_CK(cudaGetLastError());
         if ((rc = exchange(c, s, U, G, MT_XCHG_UNIQUE))) return rc;
