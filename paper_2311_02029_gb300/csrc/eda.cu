@@ -354,43 +354,66 @@ struct BucketStats {
     unsigned int maxn, maxE, err;
 };
 
+// Per-pair checks and the buckets' statistics. Every count and maximum is gathered per CTA in
+// shared memory (32-bit) and reaches the global statistics once per CTA: class counts and
+// maximum thresholds follow from the per-threshold counts.
 __global__ void k_bucket_count(const uint64_t *roff, uint64_t n_reads, const uint64_t *woff,
                                const uint32_t *pair_read, const uint16_t *E, uint64_t n_pairs,
                                BucketStats *st) {
-    __shared__ unsigned long long sc[MAX_CLASSES], sb[33], se[E_KEYS];
-    for (int i = threadIdx.x; i < MAX_CLASSES; i += blockDim.x) sc[i] = 0;
-    for (int i = threadIdx.x; i < 33; i += blockDim.x) sb[i] = 0;
+    __shared__ unsigned int se[E_KEYS], sb[33], s_cmaxn[MAX_CLASSES], s_bmaxE[33], s_err;
     for (int i = threadIdx.x; i < (int)E_KEYS; i += blockDim.x) se[i] = 0;
+    for (int i = threadIdx.x; i < 33; i += blockDim.x) { sb[i] = 0; s_bmaxE[i] = 0; }
+    for (int i = threadIdx.x; i < MAX_CLASSES; i += blockDim.x) s_cmaxn[i] = 0;
+    if (threadIdx.x == 0) s_err = 0;
     __syncthreads();
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_pairs;
          p += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t r = pair_read[p];
-        if (r >= n_reads) { atomicOr(&st->err, ERR_BAD_PAIR); continue; }
-        uint64_t n64 = roff[r + 1] - roff[r];
+        if (r >= n_reads) { s_err = ERR_BAD_PAIR; continue; }
+        const uint64_t r0 = roff[r], r1 = roff[r + 1];
+        uint64_t n64 = r1 - r0;
         uint32_t e = E[p];
         uint64_t L = woff[p + 1] - woff[p];
-        if (roff[r + 1] < roff[r] || n64 > MT_MAX_READ_LEN || e > MT_MAX_E || L != n64 + 2ull * e) {
-            atomicOr(&st->err, ERR_BAD_PAIR);
+        if (r1 < r0 || n64 > MT_MAX_READ_LEN || e > MT_MAX_E || L != n64 + 2ull * e) {
+            s_err = ERR_BAD_PAIR;
             continue;
         }
         uint32_t n = (uint32_t)n64;
-        uint32_t c = e_class(e), b = (n + 31) / 32;
-        atomicAdd(&sc[c], 1ull);
-        atomicAdd(&sb[b], 1ull);
-        atomicAdd(&se[e], 1ull);
-        atomicMax(&st->cls_maxn[c], n);
-        atomicMax(&st->cls_maxE[c], e);
-        atomicMax(&st->bkt_maxE[b], e);
-        atomicMax(&st->maxn, n);
-        atomicMax(&st->maxE, e);
+        uint32_t b = (n + 31) / 32;
+        atomicAdd(&se[e], 1u);
+        atomicAdd(&sb[b], 1u);
+        atomicMax(&s_cmaxn[e_class(e)], n);
+        atomicMax(&s_bmaxE[b], e);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < MAX_CLASSES; i += blockDim.x)
-        if (sc[i]) atomicAdd(&st->cls_count[i], sc[i]);
-    for (int i = threadIdx.x; i < 33; i += blockDim.x)
-        if (sb[i]) atomicAdd(&st->bkt_count[i], sb[i]);
+    if (threadIdx.x == 0) {
+        if (s_err) atomicOr(&st->err, s_err);
+        unsigned int maxn = 0, maxE = 0;
+        for (int c = 0; c < MAX_CLASSES; c++) {
+            if (s_cmaxn[c]) atomicMax(&st->cls_maxn[c], s_cmaxn[c]);
+            maxn = max(maxn, s_cmaxn[c]);
+        }
+        for (int e = 0; e < (int)E_KEYS; e++) if (se[e]) maxE = e;
+        if (maxn) atomicMax(&st->maxn, maxn);
+        if (maxE) atomicMax(&st->maxE, maxE);
+    }
+    if (threadIdx.x < MAX_CLASSES) {   // class c: its thresholds' counts and largest threshold
+        const int c = threadIdx.x;
+        unsigned long long cnt = 0;
+        unsigned int me = 0;
+        for (int e = 0; e < (int)E_KEYS; e++)
+            if ((int)e_class(e) == c && se[e]) { cnt += se[e]; me = e; }
+        if (cnt) {
+            atomicAdd(&st->cls_count[c], cnt);
+            atomicMax(&st->cls_maxE[c], me);
+        }
+    }
+    for (int i = threadIdx.x; i < 33; i += blockDim.x) {
+        if (sb[i]) atomicAdd(&st->bkt_count[i], (unsigned long long)sb[i]);
+        if (s_bmaxE[i]) atomicMax(&st->bkt_maxE[i], s_bmaxE[i]);
+    }
     for (int i = threadIdx.x; i < (int)E_KEYS; i += blockDim.x)
-        if (se[i]) atomicAdd(&st->e_count[i], se[i]);
+        if (se[i]) atomicAdd(&st->e_count[i], (unsigned long long)se[i]);
 }
 
 // Segment keys of the scatter: the plain form's read-word buckets; for the batched form the
@@ -400,27 +423,34 @@ __global__ void k_bucket_count(const uint64_t *roff, uint64_t n_reads, const uin
 // are O(n), and coarser segments keep neighbouring pairs' windows together).
 enum ScatterKey : int { KEY_WORDS = 0, KEY_E = 1, KEY_CLASS = 2 };
 
-// scatter pair ids into segments of one key; cursor[] starts at the segment starts.
-// Warp-aggregated per key.
+// Scatters pair ids into segments of one key; cursor[] starts at the segment starts. A CTA takes
+// tiles of one pair a thread: the tile's pairs are ranked per key in shared memory, the tile
+// reserves each key's range with one global add, and every pair goes to its place (the order
+// within a segment changes no result).
 __global__ void k_bucket_scatter(const uint64_t *roff, const uint32_t *pair_read, const uint16_t *E,
                                  uint64_t n_pairs, int key_kind, unsigned long long *cursor,
                                  uint32_t *perm) {
+    __shared__ unsigned int s_cnt[E_KEYS];
+    __shared__ unsigned long long s_base[E_KEYS];
+    const uint32_t nkeys = key_kind == KEY_E ? E_KEYS : key_kind == KEY_CLASS ? MAX_CLASSES : 33;
     for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x; p0 < n_pairs; p0 += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t p = p0 + threadIdx.x;
-        bool ok = p < n_pairs;
-        uint32_t key = 0xFFFFFFFFu;
+        const uint64_t p = p0 + threadIdx.x;
+        const bool ok = p < n_pairs;
+        uint32_t key = 0;
         if (ok) {
-            uint32_t r = pair_read[p];
-            uint32_t n = (uint32_t)(roff[r + 1] - roff[r]);
+            const uint32_t r = pair_read[p];
+            const uint32_t n = (uint32_t)(roff[r + 1] - roff[r]);
             key = key_kind == KEY_E ? (uint32_t)E[p] : key_kind == KEY_CLASS ? e_class(E[p]) : (n + 31) / 32;
         }
-        unsigned peers = __match_any_sync(FULL, key);
-        uint32_t lane = threadIdx.x & 31u;
-        uint32_t leader = __ffs(peers) - 1;
-        unsigned long long base = 0;
-        if (ok && lane == leader) base = atomicAdd(&cursor[key], (unsigned long long)__popc(peers));
-        base = __shfl_sync(FULL, base, leader);
-        if (ok) perm[base + __popc(peers & ((1u << lane) - 1))] = (uint32_t)p;
+        for (uint32_t i = threadIdx.x; i < nkeys; i += blockDim.x) s_cnt[i] = 0;
+        __syncthreads();
+        const uint32_t rank = ok ? atomicAdd(&s_cnt[key], 1u) : 0u;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nkeys; i += blockDim.x)
+            if (s_cnt[i]) s_base[i] = atomicAdd(&cursor[i], (unsigned long long)s_cnt[i]);
+        __syncthreads();
+        if (ok) perm[s_base[key] + rank] = (uint32_t)p;
+        __syncthreads();   // s_cnt and s_base are reused by the next tile
     }
 }
 
