@@ -1650,8 +1650,12 @@ __global__ void k_maxlen(const uint64_t *roff, uint64_t n_reads, uint64_t n_base
         uint64_t n = b - a;
         mx = max(mx, (unsigned int)umin64(n, 0xFFFFFFFFull));
     }
-    atomicMax(&ctr->maxn, mx);
-    if (bad) atomicOr(&ctr->err, ERR_BAD_OFFSETS);
+    mx = __reduce_max_sync(FULL, mx);   // one atomic a warp
+    bad = __any_sync(FULL, bad);
+    if ((threadIdx.x & 31u) == 0) {
+        atomicMax(&ctr->maxn, mx);
+        if (bad) atomicOr(&ctr->err, ERR_BAD_OFFSETS);
+    }
 }
 
 }  // namespace mt
