@@ -55,6 +55,8 @@ static constexpr int FB_THREADS = 256;
 template <typename HitT, bool W11 = false>
 struct WarpSmem {
     unsigned long long stat[4];     // the warp's minimizers, matches, list occurrences, stored locations
+    uint32_t nmr;                   // minimizers of the current read
+    uint32_t pad_;
     uint64_t rd[RDW];               // packed read
     HitT hits[HCAP];                // seed-match keys of the read
     union {                         // the tiles of a read, then its location walk
@@ -689,6 +691,7 @@ __global__ void __launch_bounds__(SEED_THREADS, (SeedLean<HK32, COUNT, W11>::cta
         const uint32_t nwin = n - k - w + 2, nk = n - k;
         uint32_t H = 0;
         bool ovf = COUNT;   // counting only from the start
+        if (lane == 0) ws.nmr = 0;
         int32_t carry = -1;
         constexpr bool w11 = W11;
         const uint32_t tile = w11 ? W11_TILE : TILE;
@@ -785,6 +788,7 @@ __global__ void __launch_bounds__(SEED_THREADS, (SeedLean<HK32, COUNT, W11>::cta
             }
             }
             __syncwarp();
+            if (lane == 0) ws.nmr += nm;
             if (!LEAN) st_mins += nm;
             else if (lane == 0) ws.stat[0] += nm;
             if (MULTI) {
@@ -1044,7 +1048,7 @@ __global__ void __launch_bounds__(SEED_THREADS, (SeedLean<HK32, COUNT, W11>::cta
             }
             if (rank < CSTORE) {
                 Cluster c;
-                c.hkey = hf.wide(hk_i); c.seeds = seeds_i; c.pad = 0;
+                c.hkey = hf.wide(hk_i); c.seeds = seeds_i; c.pad = ws.nmr;
                 A.clus[r * CSTORE + rank] = c;
             }
         }
@@ -1137,7 +1141,7 @@ k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uin
 #pragma unroll
                 for (uint32_t i = 0; i < 4; i++) {
                     if (k4[i] && taken < top_n) {
-                        const uint32_t bin = BINS - 1 - min(c4[i].seeds, BINS - 1);
+                        const uint32_t bin = min(c4[i].pad > c4[i].seeds ? c4[i].pad - c4[i].seeds : 0u, BINS - 1);
                         bins |= (uint64_t)bin << (6 * taken);
                         cand[r * top_n + taken++] = c4[i];
                     }
@@ -1145,7 +1149,7 @@ k_select(const IoBlock *io, const uint32_t *qcnt, const Cluster *clus, const uin
                 for (uint32_t i = 4; i < lim && taken < top_n; i++) {
                     Cluster c = clus[r * CSTORE + i];
                     if (keep[hk_genome(c.hkey)]) {
-                        const uint32_t bin = BINS - 1 - min(c.seeds, BINS - 1);
+                        const uint32_t bin = min(c.pad > c.seeds ? c.pad - c.seeds : 0u, BINS - 1);
                         bins |= (uint64_t)bin << (6 * taken);
                         cand[r * top_n + taken++] = c;
                     }
