@@ -1099,12 +1099,14 @@ __global__ void k_mask(const unsigned long long *hits, uint32_t G, uint32_t num,
 }
 
 // ---- candidate selection ----------------------------------------------------------------------
-// A tile's candidates enter the compact list ordered by seed count (most seeds first, a
-// counting sort over 64 bins in shared memory): a location holding nearly all of a read's seeds
-// is usually a near-exact match whose approximation ends in a step or two, one holding few is
-// usually a divergent genome walked to E + 1 obstacles, so a warp of the approximation kernel
-// that takes consecutive candidates walks them for similar numbers of steps. The order of the
-// list changes no result (each distance goes to its candidate's slot).
+// A tile's candidates enter the compact list ordered by missing seeds: the read's minimizers
+// (kept by the seeding kernel in the location record's spare word) minus the location's seeds,
+// fewest first, a counting sort over 64 bins in shared memory. A location holding nearly all of
+// its read's minimizers is usually a near-exact match whose approximation ends in a step or
+// two, one missing many a divergent genome walked to E + 1 obstacles, so a warp of the
+// approximation kernel that takes consecutive candidates walks them for similar numbers of
+// steps, for reads of any length. The order of the list changes no result (each distance goes
+// to its candidate's slot).
 static constexpr int SELECT_CTAS = 6;   // resident k_select CTAs an SM (40 registers)
 
 __global__ void __launch_bounds__(256, SELECT_CTAS)

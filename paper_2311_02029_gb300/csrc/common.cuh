@@ -184,7 +184,7 @@ struct IoBlock {
 struct Cluster {
     uint64_t hkey;     // hit key of its first match (genome, rel, first diagonal)
     uint32_t seeds;
-    uint32_t pad;
+    uint32_t pad;      // seeding pass: the read's minimizer count (candidate order); else 0
 };
 
 // Word index of packed sequence i for base offsets relative to off0.
