@@ -377,9 +377,10 @@ def serving_sample(mt, ix, reads, c, seconds, torch, pinned_seq=None):
         nb = int(np.prod(shape)) * np.dtype(dtype).itemsize
         return torch.empty(nb, dtype=torch.uint8).pin_memory().numpy().view(dtype).reshape(shape)
 
-    def new_out():
-        return dict(taxon=arr((cap,), np.int32), nloc=arr((cap,), np.uint8), locs=arr((cap, top_n), mt.LOC_DTYPE),
-                    genome_hits=arr((G,), np.uint64), abundance=arr((G,), np.float64))
+    def new_out():   # a request's buffers: its rebased offsets and its outputs
+        return dict(off=arr((cap + 1,), np.uint64), taxon=arr((cap,), np.int32), nloc=arr((cap,), np.uint8),
+                    locs=arr((cap, top_n), mt.LOC_DTYPE), genome_hits=arr((G,), np.uint64),
+                    abundance=arr((G,), np.float64))
     src = reads.seq if pinned_seq is None else pinned_seq
     owner = {}
 
@@ -412,9 +413,10 @@ def serving_sample(mt, ix, reads, c, seconds, torch, pinned_seq=None):
         sz = int(min(sz, reads.n))
         a = int(rng.integers(0, reads.n - sz + 1))
         b0, b1 = int(reads.offsets[a]), int(reads.offsets[a + sz])
-        off = (reads.offsets[a:a + sz + 1] - np.uint64(b0)).astype(np.uint64)
         with lock:
             buf = free_outs.pop() if free_outs else new_out()
+        off = buf["off"][:sz + 1]
+        np.subtract(reads.offsets[a:a + sz + 1], np.uint64(b0), out=off, dtype=np.uint64)
         rid = srv.submit(src[b0:b1], off, out=buf)
         with lock:
             owner[rid] = buf
