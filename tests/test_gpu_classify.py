@@ -110,6 +110,24 @@ def test_clade_workload_general_window_path(mt):
     compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
 
 
+@pytest.mark.parametrize("w", [11, 9])
+def test_more_genomes_than_shared_counters(mt, w):
+    """4,200 genomes of 2 kb (clades of 10): more genome counters than the seeding kernel keeps
+    in shared memory, so counts and unique reads go to global memory; 32-bit match keys, the
+    block path (w = 11) and the general one (w = 9). Outputs equal the oracle's."""
+    c = gen.config(2, n_genomes=4200, genome_len=2_000, clade_size=10, n_reads=4_000, seed=63, w=w)
+    g = gen.make_genomes(c)
+    r = gen.make_reads(c, g)
+    ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
+    prm = _params(c)
+    ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=8)
+    out = mt.classify(ix, r.seq, r.offsets, **prm)
+    compare_classify(out, ref)
+    assert (ref["taxon"] >= 0).mean() > 0.5 and ref["genome_hits"].astype(bool).sum() > 1000
+    ix.close()
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_clade_workload(mt, clade, mode):
     c, g, r, ix, oix = clade
