@@ -110,14 +110,28 @@ def test_clade_workload_general_window_path(mt):
     compare_classify(mt.classify(ix, r.seq, r.offsets, **prm), ref)
 
 
+@pytest.mark.parametrize("long_genome", [False, True])
 @pytest.mark.parametrize("w", [11, 9])
-def test_more_genomes_than_shared_counters(mt, w):
+def test_more_genomes_than_shared_counters(mt, w, long_genome):
     """4,200 genomes of 2 kb (clades of 10): more genome counters than the seeding kernel keeps
-    in shared memory, so counts and unique reads go to global memory; 32-bit match keys, the
-    block path (w = 11) and the general one (w = 9). Outputs equal the oracle's."""
+    in shared memory, so counts and unique reads go to global memory; the block path (w = 11)
+    and the general one (w = 9); 32-bit match keys, or 64-bit ones with one more genome of
+    4.2 Mb (its diagonals and 4,201 genome ids do not fit 32 bits). Outputs equal the oracle's."""
     c = gen.config(2, n_genomes=4200, genome_len=2_000, clade_size=10, n_reads=4_000, seed=63, w=w)
     g = gen.make_genomes(c)
+    if long_genome:
+        rng = np.random.default_rng(64)
+        extra = gen.ascii_of(rng.integers(0, 4, 4_200_000, dtype=np.uint8))
+        g = gen.Genomes(seq=np.concatenate([g.seq, extra]),
+                        offsets=np.append(g.offsets, g.offsets[-1] + np.uint64(len(extra))).astype(np.uint64),
+                        clade=np.append(g.clade, g.clade.max() + 1).astype(np.int32))
     r = gen.make_reads(c, g)
+    if long_genome:   # the first 300 reads: exact copies from the long genome, both strands
+        off0 = int(g.offsets[-2])
+        for i in range(300):
+            p = off0 + int(rng.integers(0, len(extra) - 150))
+            seg = g.seq[p:p + 150]
+            r.seq[int(r.offsets[i]):int(r.offsets[i]) + 150] = gen.revcomp_ascii(seg) if i % 2 else seg
     ix = mt.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
     oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
     prm = _params(c)
