@@ -181,3 +181,16 @@ def test_genome_sharded_exchanges_over_two_gloo_ranks(tmp_path):
         assert x["wstart"] == [-1] * 4 + [-2] * 4
         assert x["dist"] == [3] * 4 + [4] * 4
         assert x["hold"] == [1, 1, 2, 0]                              # genome 2 held twice: refused
+
+
+def test_seeding_counters_are_dropped_when_the_kernel_sources_change(monkeypatch):
+    """The stored ncu counters of the seeding kernel (traffic and instructions per read) are
+    reported only while the kernel's sources hash to the value stored with them."""
+    sys.path.insert(0, ROOT)
+    import bench
+    good = dict(bench.SEED_PROFILE)
+    monkeypatch.setattr(bench, "SEED_PROFILE", dict(good, source_sha256=bench.seed_source_sha256()))
+    traffic, inst = bench.seed_profile()
+    assert traffic == good["dram_bytes_per_read"] and inst == good["warp_inst_per_read"]
+    monkeypatch.setattr(bench, "SEED_PROFILE", dict(good, source_sha256="0" * 64))
+    assert bench.seed_profile() == (None, None)
