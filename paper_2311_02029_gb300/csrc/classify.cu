@@ -1685,8 +1685,11 @@ uint64_t fb_cap_for(uint32_t maxn, uint32_t k, uint32_t w, uint32_t max_occ) {
     return cap;
 }
 
+// host_io: the call's own copies of the host outputs and inputs are carved too (reads_in_ws:
+// the reads' bytes as well; a call that uploads them before its layout is known keeps them in
+// an allocation of their own).
 Layout plan_layout(const mt_index *ix, uint64_t n_bases, uint64_t n_reads, uint32_t top_n, uint32_t maxn,
-                   uint32_t max_occ, bool host_io) {
+                   uint32_t max_occ, bool host_io, bool reads_in_ws = true) {
     Layout L{};
     Carver c;
     L.rw_words = (n_bases >> 5) + n_reads + 2;
@@ -1713,7 +1716,7 @@ Layout plan_layout(const mt_index *ix, uint64_t n_bases, uint64_t n_reads, uint3
         L.taxon = c.take<int32_t>(n_reads);
         L.nloc = c.take<uint8_t>(n_reads);
         L.locs = c.take<mt_loc>(n_reads * top_n);
-        L.reads = c.take<uint8_t>(n_bases + 16);
+        if (reads_in_ws) L.reads = c.take<uint8_t>(n_bases + 16);
         L.roff = c.take<uint64_t>(n_reads + 1);
     }
     L.total = c.off + 256;
@@ -2009,18 +2012,74 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     const bool host_io = !device_ptrs;
     if (stats) memset(stats, 0, sizeof(*stats));
 
-    // longest read and offset checks, on the device (host offsets are copied there first)
+    // Host batches: the offsets and the reads' bytes go to allocations of their own, the bytes
+    // in chunks on a second stream that start at once, so that they move while the offsets
+    // are checked below; the seeding of a chunk waits only for its own bytes.
+    uint64_t *d_roff = nullptr;
+    uint8_t *d_reads = nullptr;
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
+    std::vector<uint64_t> chunk_r;
+    auto release = [&]() {
+        if (cs) cudaStreamSynchronize(cs);
+        for (auto e : chunk_ev) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+        if (d_roff) dfree(d_roff, s);
+        if (d_reads) dfree(d_reads, s);
+    };
     uint32_t maxn = 0;
     uint64_t off0 = 0, launches = 0;
-    uint64_t *d_roff = nullptr;   // host batches: the device copy of the offsets
-    if (n_reads) {
-        if (host_io) {
-            off0 = offsets[0];
-            if ((rc = dalloc((void **)&d_roff, (n_reads + 1) * 8, s))) return rc;
-            MT_CK(cudaMemcpyAsync(d_roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (host_io && n_reads) {
+        off0 = offsets[0];
+        if ((rc = dalloc((void **)&d_roff, (n_reads + 1) * 8, s))) return rc;
+        if ((rc = dalloc((void **)&d_reads, n_bases + 16, s))) { release(); return rc; }
+        MT_CK(cudaMemcpyAsync(d_roff, offsets, (n_reads + 1) * 8, cudaMemcpyHostToDevice, s));
+        // chunk i: reads [chunk_r[i], chunk_r[i+1]), its bytes copied on cs, then chunk_ev[i + 1].
+        // The copies queue behind the offsets' copy (one copy engine takes a direction's copies
+        // in issue order) and the first chunks are small (16 MB, doubling), so that seeding
+        // starts soon after the offsets are checked. The offsets are not checked yet (k_maxlen
+        // below does that, and a bad batch returns before any kernel reads the bytes), so every
+        // copy is clamped to the n_bases buffer.
+        const uint64_t span = offsets[n_reads] >= off0 ? offsets[n_reads] - off0 : 0;
+        const uint64_t chunk = std::max<uint64_t>(32ull << 20, span / 16);
+        if (span > chunk) {
+            int e_ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+            cudaEvent_t ready = nullptr;
+            e_ok = e_ok && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
+            if (ready) chunk_ev.push_back(ready);
+            // the copies follow the allocations, which are ordered on s
+            e_ok = e_ok && cudaEventRecord(ready, s) == cudaSuccess && cudaStreamWaitEvent(cs, ready, 0) == cudaSuccess;
+            chunk_r.push_back(0);
+            uint64_t csz = std::min<uint64_t>(16ull << 20, chunk);
+            for (uint64_t rb = 0; e_ok && rb < n_reads;) {
+                const uint64_t limit = offsets[rb] + csz;
+                csz = std::min<uint64_t>(csz * 2, chunk);
+                uint64_t re = (uint64_t)(std::upper_bound(offsets + rb + 1, offsets + n_reads + 1, limit) - offsets) - 1;
+                if (re <= rb) re = rb + 1;
+                cudaEvent_t ev = nullptr;
+                e_ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+                if (ev) chunk_ev.push_back(ev);
+                const uint64_t b0 = std::min(offsets[rb], n_bases);
+                const uint64_t b1 = std::min(std::max(offsets[re], b0), n_bases);
+                if (e_ok && b1 > b0)
+                    e_ok = cudaMemcpyAsync(d_reads + b0, reads + b0, b1 - b0, cudaMemcpyHostToDevice, cs) == cudaSuccess;
+                e_ok = e_ok && cudaEventRecord(ev, cs) == cudaSuccess;
+                chunk_r.push_back(re);
+                rb = re;
+            }
+            if (!e_ok) {
+                cuda_ok(cudaGetLastError(), "chunked read copies");
+                release();
+                return MT_ECUDA;
+            }
+        } else if (n_bases) {
+            MT_CK(cudaMemcpyAsync(d_reads, reads, n_bases, cudaMemcpyHostToDevice, s));
         }
+    }
+    // longest read and offset checks, on the device
+    if (n_reads) {
         Counters *pre = nullptr;
-        if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) { if (d_roff) dfree(d_roff, s); return rc; }
+        if ((rc = dalloc((void **)&pre, sizeof(Counters), s))) { release(); return rc; }
         MT_CK(cudaMemsetAsync(pre, 0, sizeof(Counters), s));
         unsigned blocks = (unsigned)std::min<uint64_t>((n_reads + 255) / 256, (uint64_t)sm_count() * 4);
         k_maxlen<<<blocks, 256, 0, s>>>(host_io ? d_roff : offsets, n_reads, n_bases, pre);
@@ -2031,18 +2090,18 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
         if (!host_io) MT_CK(cudaMemcpyAsync(&off0, offsets, 8, cudaMemcpyDeviceToHost, s));
         MT_CK(cudaStreamSynchronize(s));
         dfree(pre, s);
-        if (h.err) { if (d_roff) dfree(d_roff, s); return MT_EINVAL; }
+        if (h.err) { release(); return MT_EINVAL; }
         maxn = h.maxn;
     }
     const uint32_t maxE = edit_threshold(maxn, p->e_abs, p->e_permille);
     if (maxn > MT_MAX_READ_LEN || maxE > MT_MAX_E) {
-        if (d_roff) dfree(d_roff, s);
+        release();
         return MT_EINVAL;
     }
 
-    Layout L = plan_layout(ix, n_bases, n_reads, top_n, std::max<uint32_t>(maxn, 1), p->max_occ, host_io);
+    Layout L = plan_layout(ix, n_bases, n_reads, top_n, std::max<uint32_t>(maxn, 1), p->max_occ, host_io, false);
     unsigned char *ws = nullptr;
-    if ((rc = dalloc((void **)&ws, L.total, s))) { if (d_roff) dfree(d_roff, s); return rc; }
+    if ((rc = dalloc((void **)&ws, L.total, s))) { release(); return rc; }
     auto P = [&](size_t off) { return (void *)(ws + off); };
     IoBlock hio;
     hio.reads = reads;
@@ -2054,57 +2113,13 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     hio.taxon = taxon;
     hio.nloc = nloc;
     hio.locs = locs;
-    // Host reads go up in chunks on a second stream; the seeding of a chunk waits only for its
-    // own bytes, so the copy of the next chunk overlaps it.
-    cudaStream_t cs = nullptr;
-    std::vector<cudaEvent_t> chunk_ev;
-    std::vector<uint64_t> chunk_r;
-    auto release = [&]() {
-        for (auto e : chunk_ev) cudaEventDestroy(e);
-        if (cs) cudaStreamDestroy(cs);
-        if (d_roff) dfree(d_roff, s);
-    };
     if (host_io) {
-        hio.reads = (const uint8_t *)P(L.reads);
+        hio.reads = d_reads;
         hio.roff = n_reads ? d_roff : (const uint64_t *)P(L.roff);
         hio.taxon = (int32_t *)P(L.taxon);
         hio.nloc = (uint8_t *)P(L.nloc);
         hio.locs = locs ? (mt_loc *)P(L.locs) : nullptr;
         if (!n_reads) MT_CK(cudaMemcpyAsync((void *)hio.roff, offsets, 8, cudaMemcpyHostToDevice, s));
-        const uint64_t span = n_reads ? offsets[n_reads] - off0 : 0;
-        const uint64_t chunk = std::max<uint64_t>(32ull << 20, span / 16);
-        if (span > chunk) {
-            int e_ok = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
-            cudaEvent_t ready = nullptr;
-            e_ok = e_ok && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess;
-            if (ready) chunk_ev.push_back(ready);
-            // the copies follow the workspace allocation and the offsets, which are ordered on s
-            e_ok = e_ok && cudaEventRecord(ready, s) == cudaSuccess && cudaStreamWaitEvent(cs, ready, 0) == cudaSuccess;
-            chunk_r.push_back(0);
-            for (uint64_t rb = 0; e_ok && rb < n_reads;) {
-                const uint64_t limit = offsets[rb] + chunk;
-                uint64_t re = (uint64_t)(std::upper_bound(offsets + rb + 1, offsets + n_reads + 1, limit) - offsets) - 1;
-                if (re <= rb) re = rb + 1;
-                cudaEvent_t ev = nullptr;
-                e_ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
-                if (ev) chunk_ev.push_back(ev);
-                const uint64_t b0 = offsets[rb], b1 = offsets[re];
-                if (e_ok && b1 > b0)
-                    e_ok = cudaMemcpyAsync((uint8_t *)hio.reads + b0, reads + b0, b1 - b0, cudaMemcpyHostToDevice, cs) == cudaSuccess;
-                e_ok = e_ok && cudaEventRecord(ev, cs) == cudaSuccess;
-                chunk_r.push_back(re);
-                rb = re;
-            }
-            if (!e_ok) {
-                cudaStreamSynchronize(cs);
-                release();
-                dfree(ws, s);
-                cuda_ok(cudaGetLastError(), "chunked read copies");
-                return MT_ECUDA;
-            }
-        } else if (n_bases) {
-            MT_CK(cudaMemcpyAsync((void *)hio.reads, reads, n_bases, cudaMemcpyHostToDevice, s));
-        }
     }
     hio.vec_ok = ((uintptr_t)hio.reads & 15u) == 0;
     MT_CK(cudaMemcpyAsync(P(L.io), &hio, sizeof(hio), cudaMemcpyHostToDevice, s));
@@ -2142,7 +2157,7 @@ static int classify_impl(const mt_index *ix, const uint8_t *reads, uint64_t n_ba
     dfree(ws, s);
     MT_CK(cudaStreamSynchronize(s));
     release();
-    fill_stats(stats, h, n_reads, L.total, ctx.launches, stats ? ev : nullptr);
+    fill_stats(stats, h, n_reads, L.total + (d_reads ? n_bases + 16 : 0), ctx.launches, stats ? ev : nullptr);
     if (stats)
         for (auto &e : ev) cudaEventDestroy(e);
     return status_of(h.err);

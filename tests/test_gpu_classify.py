@@ -339,6 +339,26 @@ def test_host_batch_uploaded_in_chunks(mt):
     pres = mt.classify(ix, r.seq, r.offsets, out=pout, **prm)
     for k in ("taxon", "nloc", "locs", "genome_hits", "abundance"):
         assert np.array_equal(pres[k], host[k]), k
+    # The chunks start uploading before the offsets are checked: offsets past the bytes from
+    # the middle on, one decreasing offset and an end past the bytes are each refused, and the
+    # next call is unaffected.
+    bad = []
+    for edit in ("past", "decreasing", "end"):
+        off = r.offsets.copy()
+        if edit == "past":
+            off[300_000:] += np.uint64(10 ** 9)
+        elif edit == "decreasing":
+            off[250_000] = off[250_002] + np.uint64(1)
+        else:
+            off[-1] = np.uint64(len(r.seq) + 1)
+        bad.append(off)
+    for off in bad:
+        with pytest.raises(mt.MtError) as e:
+            mt.classify(ix, r.seq, off, **prm)
+        assert e.value.status == mt.MT_EINVAL
+    again = mt.classify(ix, r.seq, r.offsets, **prm)
+    for k in ("taxon", "nloc", "locs", "genome_hits", "abundance"):
+        assert np.array_equal(again[k], host[k]), k
     oix = oracle.Index(g.seq, g.offsets, c["k"], c["w"], c["canonical"])
     ref = oracle.classify(oix, r.seq, r.offsets, oracle_params(prm), threads=16)
     compare_classify(host, ref)
